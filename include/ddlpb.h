@@ -1,0 +1,168 @@
+/*
+ * ddlpb.h -- C ABI of the GB300 (sm_103a) ddLPB energy + analytical force library.
+ *
+ * The method: Jha, Nottoli, Mikhalev, Quan, Stamm, "Linear scaling computation
+ * of forces for the domain-decomposition linear Poisson-Boltzmann method"
+ * (arXiv:2203.00552).  A solute is a union of M atom-centred balls
+ * (Sec. 1; van der Waals radii, or solvent-accessible radii = vdW + 1.4 A)
+ * carrying point charges (Eq. rho_definition).  Each ball carries real
+ * spherical-harmonic expansions up to degree lmax of the reaction potential
+ * psi_r and the extended potential psi_e (Sec. 2.2), sampled on a Lebedev grid.
+ * The library assembles and solves the block system L X = g (Eq. AXg), the
+ * adjoint system L* X_adj = Q (Eqs. adjoint_system, AstarXg), and returns the
+ * solvation energy (Eq. energy_computation) and forces (Eq. force_lpb).
+ *
+ * Units: atomic units throughout.  Positions and radii in Bohr, charges in e,
+ * kappa in 1/Bohr, energies in Hartree, forces in Hartree/Bohr.  The solute
+ * permittivity eps_1 is 1 (Sec. 4).
+ *
+ * Memory: every pointer argument names memory that the caller owns; the
+ * library copies inputs during the call and never keeps a caller pointer.
+ * Functions whose name ends in _device take CUDA device pointers (on the device
+ * that was current at ddlpb_setup); all others take host pointers.  The
+ * context owns all device memory it allocates and frees it in ddlpb_free.
+ * Every call runs on the CUDA stream given in ddlpb_options.cuda_stream (NULL:
+ * the legacy default stream) and returns only after its results are
+ * available to the caller.
+ *
+ * Errors: every call returns a ddlpb_status and never aborts the process.  On
+ * error, ddlpb_last_error(ctx) returns a message (for a failed setup the
+ * message is available through ddlpb_last_setup_error()).  A context whose
+ * call returned DDLPB_ECUDA must be freed.
+ */
+#ifndef DDLPB_H
+#define DDLPB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DDLPB_API __attribute__((visibility("default")))
+#else
+#define DDLPB_API
+#endif
+
+typedef struct ddlpb_ctx ddlpb_ctx;
+
+typedef enum { DDLPB_VDW = 0, DDLPB_SAS = 1 } ddlpb_surface;
+
+typedef enum {
+    DDLPB_OK = 0,
+    DDLPB_EINVAL = 1,    /* invalid argument (size, radius, lmax vs grid, NaN ...) */
+    DDLPB_ENOMEM = 2,    /* device allocation failed */
+    DDLPB_ENOTCONV = 3,  /* outer solve did not reach tol within max_iter */
+    DDLPB_ECUDA = 4,     /* CUDA runtime error; the context must be freed */
+    DDLPB_EORDER = 5     /* call order violated (e.g. forces before adjoint) */
+} ddlpb_status;
+
+typedef enum { DDLPB_FP64 = 0, DDLPB_MIXED = 1 } ddlpb_precision;
+
+typedef struct {
+    double eta;          /* width of the smooth switch chi_eta (Eq. regular_char_function); default 0.1 */
+    double tol;          /* relative residual ||g - L X|| / ||g|| of both solves; default 1e-8 */
+    int max_iter;        /* cap on outer (FP64) Krylov iterations; default 500 */
+    int gmres_restart;   /* Krylov basis size before restart; default 40 */
+    int precision;       /* ddlpb_precision; default DDLPB_FP64 */
+    int fmm_order;       /* 0: direct summation of the dense coupling (the only mode of this build) */
+    void* cuda_stream;   /* cudaStream_t the context launches on; NULL = legacy default stream */
+} ddlpb_options;
+
+typedef struct {
+    int n_atoms;
+    int lmax;
+    int n_lebedev;
+    long long n_neighbour_pairs;   /* sum_i |N_i| (Sec. 2.2) */
+    long long n_hits;              /* (i, n, j) with omega_ij^eta(x_i^n) > 0: nonzeros of A/B rows */
+    long long n_external;          /* grid points with chi_i^eta(x_i^n) > 0 */
+    int solve_iterations;          /* Krylov iterations of the last primal solve */
+    int adjoint_iterations;        /* Krylov iterations of the last adjoint solve */
+    double solve_residual;         /* final FP64 relative residual of the primal solve */
+    double adjoint_residual;       /* final FP64 relative residual of the adjoint solve */
+    int refinement_steps;          /* FP64 refinement steps of the last solve (mixed precision) */
+} ddlpb_info;
+
+/* Fill *opt with the defaults listed above. */
+DDLPB_API void ddlpb_default_options(ddlpb_options* opt);
+
+/*
+ * Build the discrete problem of Sec. 2.2 for one solute and compute the
+ * right-hand side g = [G0 + F0; F0] (Eqs. definition_of_G_0, definition_of_F_0).
+ *   n         number of atoms M >= 1
+ *   centres   n*3 doubles, x y z of atom k at 3k..3k+2 (Bohr)
+ *   radii     n doubles (Bohr), > 0; surface == DDLPB_SAS adds the 1.4 A probe (Sec. 4)
+ *   charges   n doubles (e)
+ *   eps_solvent  relative permittivity of the solvent eps_2 > 1
+ *   kappa     Debye-Hueckel screening constant (1/Bohr), > 0
+ *   lmax      maximum degree of the expansions, 0 <= lmax <= 16
+ *   n_lebedev number of Lebedev points; one of 6, 14, 26, 38, 50, 74, 86, 110,
+ *             146, 170, 194, 230, 266, 302, 350, 434, 590, 770, with an exact
+ *             degree >= 2*lmax (so that the projections of Sec. 2.2 are exact)
+ *   opt       NULL for the defaults
+ *   out       receives the new context (NULL on error)
+ * Errors: DDLPB_EINVAL (bad sizes, NaN/Inf, coincident centres, radius <= 0,
+ * unsupported grid), DDLPB_ENOMEM, DDLPB_ECUDA.
+ */
+DDLPB_API ddlpb_status ddlpb_setup(int n, const double* centres, const double* radii, const double* charges,
+                         double eps_solvent, double kappa, int lmax, int n_lebedev,
+                         ddlpb_surface surface, const ddlpb_options* opt, ddlpb_ctx** out);
+
+/* Same as ddlpb_setup with centres, radii and charges in device memory. */
+DDLPB_API ddlpb_status ddlpb_setup_device(int n, const double* centres, const double* radii, const double* charges,
+                                double eps_solvent, double kappa, int lmax, int n_lebedev,
+                                ddlpb_surface surface, const ddlpb_options* opt, ddlpb_ctx** out);
+
+/* Solve L X = g (Eq. AXg) to the relative residual opt.tol.  Warm-starts from the
+ * previous solution of this context if there is one.  DDLPB_ENOTCONV if max_iter
+ * is reached (X then holds the last iterate). */
+DDLPB_API ddlpb_status ddlpb_solve(ddlpb_ctx* ctx);
+
+/* Solve L* X_adj = Q (Eqs. adjoint_system, AstarXg), Q_{j00} = q_j Y_00.  Requires
+ * a successful ddlpb_solve (else DDLPB_EORDER). */
+DDLPB_API ddlpb_status ddlpb_adjoint(ddlpb_ctx* ctx);
+
+/* E_s = 1/2 <X, Q> (Eq. energy_computation), Hartree, written to *e (host).
+ * Requires ddlpb_solve. */
+DDLPB_API ddlpb_status ddlpb_energy(ddlpb_ctx* ctx, double* e);
+
+/* Forces F_k = -dE_s/dx_k (Eq. force_lpb with the derivatives of Sec. 3.1),
+ * n*3 doubles in the layout of centres.  Requires ddlpb_adjoint (else
+ * DDLPB_EORDER).  f is host memory (ddlpb_forces) or device memory
+ * (ddlpb_forces_device). */
+DDLPB_API ddlpb_status ddlpb_forces(ddlpb_ctx* ctx, double* f);
+DDLPB_API ddlpb_status ddlpb_forces_device(ddlpb_ctx* ctx, double* f);
+
+/* Energy into device memory (one double). */
+DDLPB_API ddlpb_status ddlpb_energy_device(ddlpb_ctx* ctx, double* e);
+
+/*
+ * Operator access (device pointers, vectors of 2*n*(lmax+1)^2 doubles laid out
+ * as [X_r ; X_e], each block sphere-major with the (l, m) index l*l + l + m).
+ *   op = 0: y = L x        (Eq. AXg)
+ *   op = 1: y = L* x       (Eq. AstarXg)
+ *   op = 2: y = [A x_r ; B x_e]                   (Eqs. definition_of_A/B_matrix)
+ *   op = 3: y = [A^T x_r ; B^T x_e]
+ *   op = 4: y = [C1 x_r + C2 x_e ; same]          (Eqs. definition_of_C1/C2_matrix)
+ *   op = 5: y = [C1^T (x_r + x_e) ; C2^T (x_r + x_e)]
+ */
+DDLPB_API ddlpb_status ddlpb_apply_device(ddlpb_ctx* ctx, int op, const double* x, double* y);
+
+/* Copy g (op 0), X (op 1) or X_adj (op 2) into device memory y (same layout as above). */
+DDLPB_API ddlpb_status ddlpb_get_vector_device(ddlpb_ctx* ctx, int which, double* y);
+
+/* Counters and solver statistics. */
+DDLPB_API ddlpb_status ddlpb_get_info(const ddlpb_ctx* ctx, ddlpb_info* info);
+
+/* Message of the last error of ctx ("" if none). */
+DDLPB_API const char* ddlpb_last_error(const ddlpb_ctx* ctx);
+
+/* Message of the last failed ddlpb_setup/ddlpb_setup_device of this thread. */
+DDLPB_API const char* ddlpb_last_setup_error(void);
+
+/* Free every device allocation of ctx (NULL is allowed). */
+DDLPB_API void ddlpb_free(ddlpb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDLPB_H */

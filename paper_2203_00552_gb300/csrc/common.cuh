@@ -1,0 +1,364 @@
+// common.cuh -- context, error plumbing and device math shared by the ddLPB kernels.
+//
+// Method: Jha, Nottoli, Mikhalev, Quan, Stamm, arXiv:2203.00552 (ddLPB energy and
+// forces).  Section / equation names below refer to that paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ddlpb.h"
+
+#define DDLPB_LMAX_MAX 16
+#define DDLPB_LT (DDLPB_LMAX_MAX + 4)   // row stride of the (l, m) coefficient tables
+
+// ---------------------------------------------------------------------------
+// Tables of the real spherical-harmonic recurrence (Sec. 2.2, Eq. definition_ylm).
+// Y_lm = sqrt(2) Q_l^m(z) Re (x+iy)^m, Y_l-m = sqrt(2) Q_l^m(z) Im (x+iy)^m,
+// Y_l0 = Q_l^0(z), with Q_l^m = P~_l^m / sin^m(theta) the fully normalised
+// associated Legendre function (no Condon-Shortley phase) divided by sin^m.
+//   Q_m^m     = qmm[m]
+//   Q_{m+1}^m = q1[m] z Q_m^m
+//   Q_l^m     = a[l][m] (z Q_{l-1}^m - b[l][m] Q_{l-2}^m)
+// kr[l] = 1/((2l+1)(2l-1)) drives the scaled k_l recurrence, si[l] the series of
+// the scaled i_l.
+struct YTab {
+    const double* a;     // [DDLPB_LT * DDLPB_LT]
+    const double* b;
+    const double* qmm;   // [DDLPB_LT]
+    const double* q1;    // [DDLPB_LT]
+};
+
+// Scratch of the force assembly, allocated on the first ddlpb_forces call.
+struct ForceScratch {
+    bool ready = false;
+    double *xir = nullptr, *xie = nullptr, *UA = nullptr, *UB = nullptr, *ch = nullptr, *Ft = nullptr;
+    double *G = nullptr, *muC = nullptr, *nu = nullptr, *muc = nullptr;
+    double4* fs = nullptr;
+    int* extpos = nullptr;
+};
+
+struct ddlpb_ctx {
+    // problem
+    int M = 0, lmax = 0, nb = 0, N = 0, degree = 0;
+    double eps1 = 1.0, eps2 = 78.54, kappa = 0.0, eta = 0.1;
+    ddlpb_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    bool solved = false, adjoint_done = false;
+    ddlpb_info info{};
+    std::vector<void*> allocs;
+
+    // geometry / tables (device)
+    double4* sph = nullptr;     // [M] x y z r (cavity radius)
+    double* q = nullptr;        // [M]
+    double4* leb = nullptr;     // [N] s_n, w_n
+    double* Y = nullptr;        // [N][nb]   Y_lm(s_n)
+    double* YT = nullptr;       // [nb][N]
+    double* ytab = nullptr;     // a | b | qmm | q1
+    YTab yt{};
+    double* Sinv = nullptr;     // [M][lmax+2] 1 / S_l(kappa r_j) (scaled i_l)
+    double* Khinv = nullptr;    // [M][lmax+2] 1 / khat_l(kappa r_j) (scaled k_l)
+    double* di = nullptr;       // [M][lmax+1] i_l'(r_j)/i_l(r_j)
+    double* dk = nullptr;       // [M][lmax+1] k_l'(r_j)/k_l(r_j)
+    double* cik = nullptr;      // [M][lmax+1] C_ik^j(l)
+    int* nbr_ptr = nullptr;     // [M+1]
+    int* nbr_idx = nullptr;
+    long long n_pairs = 0;
+    double* fval = nullptr;     // [M*N] f^i(x_i^n)
+    double* chi = nullptr;      // [M*N] chi_i^eta(x_i^n)
+    int* hit_ptr = nullptr;     // [M*N+1]
+    int* hit_j = nullptr;       // [H]
+    double* hit_w = nullptr;    // [H] omega_ij^eta(x_i^n)
+    int* thit_ptr = nullptr;    // [M+1] hits grouped by the sphere j they point at
+    int* thit_p = nullptr;      // [H] point index i*N+n
+    int* thit_h = nullptr;      // [H] index of the hit in the point-major list
+    double* thit_w = nullptr;   // [H]
+    long long H = 0;
+    int* ext_ptr = nullptr;     // [M+1] external points grouped by sphere
+    int* ext_p = nullptr;       // [E] point index i*N+n
+    double4* ext_x = nullptr;   // [E] position and chi
+    int E = 0;
+    int* src = nullptr;         // spheres with at least one external point
+    int n_src = 0;
+
+    // right-hand side and solutions (device), vectors of length nvec = 2*M*nb
+    long long nvec = 0;
+    double* g = nullptr;
+    double* X = nullptr;
+    double* Xa = nullptr;
+    double* Qv = nullptr;
+    double* psi0 = nullptr;     // [E] psi_0 at external points
+    double* dnpsi0 = nullptr;   // [E] d_n psi_0 at external points
+    double* mu0 = nullptr;      // [M][nb] C_ik C0 (multipoles of F0)
+    double* S0 = nullptr;       // [E] potential of mu0 at external points
+
+    // scratch
+    double* gm_V = nullptr;     // Krylov basis [(restart+1)][nvec]
+    double* gm_w = nullptr;     // [nvec]
+    double* gm_r = nullptr;     // [nvec]
+    double* gm_red = nullptr;   // partial reductions
+    double* gm_h = nullptr;     // [restart+2]
+    double* h_pinned = nullptr; // host pinned mirror of gm_h
+    double* mu = nullptr;       // [M][nb]
+    double* gridA = nullptr;    // [M*N]
+    double* gridB = nullptr;    // [M*N]
+    double* extA = nullptr;     // [E]
+    double* extB = nullptr;     // [E]
+    double* tmpv = nullptr;     // [nvec]
+    double* force_acc = nullptr;
+    ForceScratch fscr;
+};
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+#define DDLPB_CK(ctx, call)                                                        \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) {                                                  \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e__);      \
+            return DDLPB_ECUDA;                                                    \
+        }                                                                          \
+    } while (0)
+
+#define DDLPB_LAUNCHED(ctx, name)                                                  \
+    do {                                                                           \
+        cudaError_t e__ = cudaGetLastError();                                      \
+        if (e__ != cudaSuccess) {                                                  \
+            (ctx)->err = std::string("launch ") + name + ": " + cudaGetErrorString(e__); \
+            return DDLPB_ECUDA;                                                    \
+        }                                                                          \
+    } while (0)
+
+#define DDLPB_TRY(x)                                                               \
+    do {                                                                           \
+        ddlpb_status s__ = (x);                                                    \
+        if (s__ != DDLPB_OK) return s__;                                           \
+    } while (0)
+
+template <typename T>
+static ddlpb_status ctx_alloc(ddlpb_ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes: " +
+                 cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? DDLPB_ENOMEM : DDLPB_ECUDA;
+    }
+    c->allocs.push_back((void*)*p);
+    return DDLPB_OK;
+}
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Device math.
+
+// Stream all Y_lm(u), u = (x, y, z) a unit vector, calling f(idx, l, Y).
+template <typename T, typename F>
+__device__ __forceinline__ void ylm_stream(int lmax, T x, T y, T z, const YTab& yt, F&& f) {
+    const T SQ2 = (T)1.4142135623730951;
+    T cr = 1, ci = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) {
+            T nr = cr * x - ci * y;
+            ci = cr * y + ci * x;
+            cr = nr;
+        }
+        T q0 = (T)__ldg(yt.qmm + m);
+        T sr = SQ2 * cr, si = SQ2 * ci;
+        if (m == 0) {
+            f(0, 0, q0);
+        } else {
+            f(m * m + 2 * m, m, q0 * sr);
+            f(m * m, m, q0 * si);
+        }
+        if (m + 1 <= lmax) {
+            T q1 = (T)__ldg(yt.q1 + m) * z * q0;
+            int l = m + 1;
+            if (m == 0) f(l * l + l, l, q1);
+            else { f(l * l + l + m, l, q1 * sr); f(l * l + l - m, l, q1 * si); }
+            for (l = m + 2; l <= lmax; ++l) {
+                T q2 = (T)__ldg(yt.a + l * DDLPB_LT + m) * (z * q1 - (T)__ldg(yt.b + l * DDLPB_LT + m) * q0);
+                q0 = q1;
+                q1 = q2;
+                if (m == 0) f(l * l + l, l, q2);
+                else { f(l * l + l + m, l, q2 * sr); f(l * l + l - m, l, q2 * si); }
+            }
+        }
+    }
+}
+
+// Stream Y_lm(u) and the ambient gradient G of F(x,y,z) = Q_l^m(z) C_m(x,y),
+// whose tangential projection G - (u.G) u is the surface gradient of Y_lm at u
+// (used for Eq. derivative_ylm).  Calls f(idx, l, Y, Gx, Gy, Gz).
+template <typename T, typename F>
+__device__ __forceinline__ void ylm_grad_stream(int lmax, T x, T y, T z, const YTab& yt, F&& f) {
+    const T SQ2 = (T)1.4142135623730951;
+    T cr = 1, ci = 0, pr = 0, pi = 0;  // w^m, w^(m-1), w = x + i y
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) {
+            pr = cr;
+            pi = ci;
+            T nr = cr * x - ci * y;
+            ci = cr * y + ci * x;
+            cr = nr;
+        }
+        T fm = (T)m;
+        // d/dx Re w^m = m Re w^(m-1), d/dy Re w^m = -m Im w^(m-1)
+        // d/dx Im w^m = m Im w^(m-1), d/dy Im w^m =  m Re w^(m-1)
+        T q0 = (T)__ldg(yt.qmm + m), d0 = 0;
+        auto emit = [&](int l, T q, T d) {
+            if (m == 0) {
+                f(l * l + l, l, q, (T)0, (T)0, d);
+            } else {
+                f(l * l + l + m, l, SQ2 * q * cr, SQ2 * q * fm * pr, -SQ2 * q * fm * pi, SQ2 * d * cr);
+                f(l * l + l - m, l, SQ2 * q * ci, SQ2 * q * fm * pi, SQ2 * q * fm * pr, SQ2 * d * ci);
+            }
+        };
+        emit(m, q0, d0);
+        if (m + 1 <= lmax) {
+            T c1 = (T)__ldg(yt.q1 + m);
+            T q1 = c1 * z * q0, d1 = c1 * q0;
+            emit(m + 1, q1, d1);
+            for (int l = m + 2; l <= lmax; ++l) {
+                T a = (T)__ldg(yt.a + l * DDLPB_LT + m), b = (T)__ldg(yt.b + l * DDLPB_LT + m);
+                T q2 = a * (z * q1 - b * q0);
+                T d2 = a * (q1 + z * d1 - b * d0);
+                q0 = q1; q1 = q2;
+                d0 = d1; d1 = d2;
+                emit(l, q2, d2);
+            }
+        }
+    }
+}
+
+// Scaled modified spherical Bessel function of the first kind,
+//   S_l(x) = (2l+1)!! i_l(x) / x^l = sum_k (x^2/2)^k (2l+1)!! / (k! (2l+2k+1)!!),
+// a series of positive terms (stable for every x >= 0).
+template <typename T>
+__device__ __forceinline__ T scaled_i_series(int l, T x) {
+    T h = (T)0.5 * x * x, t = 1, s = 1;
+    const T eps = sizeof(T) == 8 ? (T)1e-17 : (T)3e-8;
+    for (int k = 1; k < 400; ++k) {
+        t *= h / (T)(k * (2 * l + 2 * k + 1));
+        s += t;
+        if (t < eps * s) break;
+    }
+    return s;
+}
+
+// Radial factors of the three bases of Sec. 2.2 at distance rho from centre j
+// (radius rj), for l = 0..lmax, written to rad[l*stride] (and their rho-
+// derivatives to drad[l*stride] when drad != nullptr):
+//   kind 0: r_l^j       = (rho/rj)^l                                      (Eq. definition_radial_scaling)
+//   kind 1: i_l ratio   = i_l(kappa rho)/i_l(kappa rj)                     (Eq. definition_of_bessel_func_first)
+//           = (rho/rj)^l S_l(kappa rho) / S_l(kappa rj)
+//   kind 2: k_l ratio   = k_l(kappa rho)/k_l(kappa rj)                     (Eq. definition_of_bessel_func_second)
+//           = exp(-kappa(rho - rj)) (rj/rho)^(l+1) khat_l(kappa rho)/khat_l(kappa rj),
+//           khat_0 = 1, khat_1 = 1 + x, khat_{l+1} = khat_l + x^2 khat_{l-1} / ((2l+1)(2l-1)).
+// inv_tab holds 1/S_l(kappa rj) (kind 1) or 1/khat_l(kappa rj) (kind 2), l = 0..lmax+1.
+template <typename T>
+__device__ __forceinline__ void radial(int kind, int lmax, T rho, T rj, T kappa, const T* inv_tab,
+                                       T* rad, T* drad, int stride) {
+    if (kind == 0) {
+        T s = rho / rj, v = 1;
+        for (int l = 0; l <= lmax; ++l) {
+            rad[l * stride] = v;
+            if (drad) drad[l * stride] = (T)l * v / rho;
+            v *= s;
+        }
+    } else if (kind == 1) {
+        T x = kappa * rho, x2 = x * x;
+        // downward recurrence S_{l-1} = S_l + x^2 S_{l+1} / ((2l+1)(2l+3)), from S_{L+2}, S_{L+1}
+        int L = lmax;
+        T s_hi = scaled_i_series<T>(L + 2, x);
+        T s_mid = scaled_i_series<T>(L + 1, x);
+        // rad[l] temporarily holds S_l(x)
+        T sp1 = s_mid, sp2 = s_hi;
+        for (int l = L; l >= 0; --l) {
+            T sl = sp1 + x2 * sp2 / (T)((2 * l + 3) * (2 * l + 5));
+            if (drad) drad[l * stride] = sp1 / sl;   // S_{l+1}/S_l
+            rad[l * stride] = sl;
+            sp2 = sp1;
+            sp1 = sl;
+        }
+        T s = rho / rj, v = 1;
+        for (int l = 0; l <= L; ++l) {
+            T sl = rad[l * stride];
+            T r = v * sl * inv_tab[l];
+            rad[l * stride] = r;
+            if (drad) drad[l * stride] = r * ((T)l / rho + kappa * kappa * rho / (T)(2 * l + 3) * drad[l * stride]);
+            v *= s;
+        }
+    } else {
+        T x = kappa * rho, x2 = x * x;
+        T e = exp(-kappa * (rho - rj));
+        T s = rj / rho, v = e * s;
+        T k0 = 1, k1 = 1 + x;
+        for (int l = 0; l <= lmax; ++l) {
+            T kl = (l == 0) ? k0 : k1;
+            T knext = (l == 0) ? k1 : k1 + x2 * k0 / (T)((2 * l + 1) * (2 * l - 1));
+            T r = v * kl * inv_tab[l];
+            rad[l * stride] = r;
+            if (drad) drad[l * stride] = r * ((T)l - (T)(2 * l + 1) * knext / kl) / rho;
+            if (l >= 1) { k0 = k1; k1 = knext; }
+            v *= s;
+        }
+    }
+}
+
+// Smooth switch chi_eta(t) of Eq. regular_char_function, with the constant of p_eta
+// read as 10 eta^2 - 15 eta + 6 (the only reading that makes chi_eta continuous).
+__device__ __forceinline__ double chi_eta(double t, double eta) {
+    if (t <= 1.0 - eta) return 1.0;
+    if (t >= 1.0) return 0.0;
+    double a = 1.0 - t;
+    double ie = 1.0 / eta;
+    double ie5 = ie * ie * ie * ie * ie;
+    return ie5 * a * a * a * (6.0 * t * t + (15.0 * eta - 12.0) * t + 10.0 * eta * eta - 15.0 * eta + 6.0);
+}
+
+__device__ __forceinline__ double dchi_eta(double t, double eta) {
+    if (t <= 1.0 - eta || t >= 1.0) return 0.0;
+    double a = 1.0 - t;
+    double ie = 1.0 / eta;
+    double ie5 = ie * ie * ie * ie * ie;
+    double poly = 6.0 * t * t + (15.0 * eta - 12.0) * t + 10.0 * eta * eta - 15.0 * eta + 6.0;
+    double dpoly = 12.0 * t + 15.0 * eta - 12.0;
+    return ie5 * (-3.0 * a * a * poly + a * a * a * dpoly);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side internal entry points (defined across the .cu files).
+ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const double* radii,
+                                  const double* charges, bool device_ptrs, int surface);
+ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose);
+ddlpb_status op_apply_AB(ddlpb_ctx* c, const double* x, double* y, bool transpose, double* gridR,
+                         double* gridE);
+ddlpb_status op_apply_C(ddlpb_ctx* c, const double* x, double* y, bool transpose, bool accumulate);
+ddlpb_status op_synthesis(ddlpb_ctx* c, const double* coef, int rows, double* grid, bool weighted);
+ddlpb_status op_yukawa_potential(ddlpb_ctx* c, const double* mu, double* phi_ext);
+ddlpb_status op_yukawa_adjoint(ddlpb_ctx* c, const double* c_ext, double* nu);
+ddlpb_status op_masked_analysis(ddlpb_ctx* c, const double* val_ext, double scale, const double* cik_scale,
+                                double* out, int out_stride, int accumulate);
+ddlpb_status op_ext_weights(ddlpb_ctx* c, const double* x, double* cext);
+ddlpb_status op_source_multipoles(ddlpb_ctx* c, const double* x, double* mu);
+ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double* x, int* iters,
+                          double* resid);
+ddlpb_status compute_forces(ddlpb_ctx* c, double* f_dev);

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP64 path): relative energy error <= 1e-10 and max force error
+<= 1e-8 Hartree/Bohr against the oracle on the same seeded inputs; every
+operator and the right-hand side element by element at 1e-11 of the vector's
+max-norm (a few hundred FP64 roundings of O(1) terms).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ddlpb as O
+from paper_2203_00552_gb300 import synth
+import paper_2203_00552_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+KAPPA = synth.KAPPA_PER_ANGSTROM / synth.ANGSTROM_TO_BOHR
+EPS = synth.EPS_SOLVENT
+DEV = "cuda:0"
+
+
+def _ctx(c, r, q, lmax, n, surface="vdw", **kw):
+    kw.setdefault("tol", 1e-13)
+    return G.Context(c, r, q, EPS, KAPPA, lmax, n, surface=surface, **kw)
+
+
+def _flat(p, X):
+    return np.asarray(X).reshape(-1)
+
+
+def _rand(nvec, seed):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    return torch.randn(nvec, generator=g, dtype=torch.float64).to(DEV)
+
+
+CASES = {
+    # name: (M, seed, kind, surface, lmax, n_lebedev)
+    "chain20_l6_110": (20, 0, "chain", "vdw", 6, 110),
+    "chain37_l5_86": (37, 5, "chain", "vdw", 5, 86),
+    "globule45_sas_l4_50": (45, 7, "globule", "sas", 4, 50),
+    "globule60_l3_38": (60, 9, "globule", "vdw", 3, 38),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    M, seed, kind, surf, lmax, n = CASES[request.param]
+    c, r, q = synth.molecule(M, seed, kind, None, surf)
+    p = O.DDLPB(c, r, q, EPS, KAPPA, lmax, n, surface=surf)
+    g = p.rhs()
+    ctx = _ctx(c, r, q, lmax, n, surf)
+    return dict(name=request.param, c=c, r=r, q=q, p=p, g=g, ctx=ctx, lmax=lmax, n=n, surf=surf)
+
+
+def test_counts_match_oracle(case):
+    p, ctx = case["p"], case["ctx"]
+    info = ctx.info()
+    assert info["n_neighbour_pairs"] == sum(len(x) for x in p.nbrs)
+    assert info["n_external"] == int((p.chi > 0).sum())
+    hits = sum(int((p.t(i, j) < 1).sum()) for i in range(p.M) for j in p.nbrs[i])
+    assert info["n_hits"] == hits
+
+
+def test_rhs_parity(case):
+    ctx, g = case["ctx"], case["g"]
+    out = torch.empty(ctx.nvec, dtype=torch.float64, device=DEV)
+    ctx.vector(0, out)
+    ref = g.reshape(-1)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("op", ["L", "LT", "AB", "ABT", "C", "CT"])
+def test_operator_parity(case, op):
+    p, ctx = case["p"], case["ctx"]
+    M, nb = p.M, p.nb
+    x = _rand(ctx.nvec, 11)
+    xn = x.cpu().numpy().reshape(2 * M, nb)
+    if op == "L":
+        ref = p.apply_L(xn)
+        code = G.OP_L
+    elif op == "LT":
+        ref = p.apply_LT(xn)
+        code = G.OP_LT
+    elif op == "AB":
+        ref = np.concatenate([p.apply_A(xn[:M]), p.apply_B(xn[M:])])
+        code = G.OP_AB
+    elif op == "ABT":
+        ref = np.concatenate([p.apply_AT(xn[:M]), p.apply_AT(xn[M:], kind="i")])
+        code = G.OP_ABT
+    elif op == "C":
+        k = p.apply_K(p.ycoef(xn[:M], xn[M:]))
+        ref = np.concatenate([k, k])
+        code = G.OP_C
+    else:
+        kt = p.apply_KT(xn[:M] + xn[M:])
+        c1 = (p.eps1 / p.eps2) * p.lidx[None, :] / p.r[:, None]
+        ref = np.concatenate([c1 * kt, -p.lexpand(p.di) * kt])
+        code = G.OP_CT
+    y = torch.empty_like(x)
+    ctx.apply(code, x, y)
+    yn = y.cpu().numpy().reshape(2 * M, nb)
+    assert np.abs(yn - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1.0)
+
+
+def test_energy_and_forces_parity(case):
+    p, ctx = case["p"], case["ctx"]
+    p.solve()
+    E_ref = p.energy()
+    p.adjoint()
+    F_ref = p.forces()
+    ctx.solve()
+    E = ctx.energy()
+    assert abs(E - E_ref) <= 1e-10 * abs(E_ref)
+    ctx.adjoint()
+    F = ctx.forces()
+    assert np.abs(F - F_ref).max() <= 1e-8
+    assert np.abs(F.sum(0)).max() <= 1e-10 * max(np.abs(F).max(), 1e-12) * F.shape[0]
+    X = torch.empty(ctx.nvec, dtype=torch.float64, device=DEV)
+    ctx.vector(1, X)
+    assert np.abs(X.cpu().numpy() - p.X.reshape(-1)).max() <= 1e-9 * np.abs(p.X).max()
+    info = ctx.info()
+    assert info["solve_residual"] <= 1e-12 and info["adjoint_residual"] <= 1e-12
+
+
+def test_single_ion_born():
+    a = 2.0 * synth.ANGSTROM_TO_BOHR
+    ctx = _ctx(np.array([[0.5, -1.0, 2.0]]), np.array([a]), np.array([1.0]), 4, 50)
+    ctx.solve()
+    E = ctx.energy()
+    ref = 1.0 / (2 * a) * (1.0 / (EPS * (1 + KAPPA * a)) - 1.0)
+    assert abs(E - ref) <= 1e-12 * abs(ref)
+    ctx.adjoint()
+    assert np.abs(ctx.forces()).max() < 1e-12
+
+
+def test_isolated_and_nested_spheres():
+    # two isolated ions (no hits) and one sphere swallowed by another (no external points)
+    c = np.array([[0.0, 0, 0], [30.0, 0, 0], [30.5, 0.2, 0.0]])
+    r = np.array([3.0, 4.0, 1.5])
+    q = np.array([0.4, -0.3, 0.2])
+    p = O.DDLPB(c, r, q, EPS, KAPPA, 4, 50)
+    p.solve()
+    p.adjoint()
+    ctx = _ctx(c, r, q, 4, 50)
+    assert ctx.info()["n_external"] == int((p.chi > 0).sum())
+    ctx.solve()
+    assert abs(ctx.energy() - p.energy()) <= 1e-10 * abs(p.energy())
+    ctx.adjoint()
+    assert np.abs(ctx.forces() - p.forces()).max() <= 1e-8
+
+
+def test_device_setup_and_outputs_match_host():
+    c, r, q = synth.molecule(12, 4, "chain")
+    h = _ctx(c, r, q, 4, 50)
+    h.solve()
+    h.adjoint()
+    d = G.Context(torch.tensor(c, device=DEV), torch.tensor(r, device=DEV), torch.tensor(q, device=DEV), EPS, KAPPA,
+                  4, 50, tol=1e-13)
+    d.solve()
+    d.adjoint()
+    e = torch.empty(1, dtype=torch.float64, device=DEV)
+    d.energy_device(e)
+    f = torch.empty((12, 3), dtype=torch.float64, device=DEV)
+    d.forces_device(f)
+    assert float(e) == h.energy()
+    assert np.array_equal(f.cpu().numpy(), h.forces())
+
+
+def test_error_paths():
+    c, r, q = synth.molecule(6, 1, "chain")
+    ctx = _ctx(c, r, q, 3, 50)
+    with pytest.raises(G.DDLPBError) as e:
+        ctx.adjoint()
+    assert e.value.status == 5
+    with pytest.raises(G.DDLPBError) as e:
+        ctx.forces()
+    assert e.value.status == 5
+    bad = _ctx(c, r, q, 3, 50, max_iter=1, tol=1e-14)
+    with pytest.raises(G.DDLPBError) as e:
+        bad.solve()
+    assert e.value.status == 3
+    rr = r.copy()
+    rr[2] = np.nan
+    with pytest.raises(G.DDLPBError) as e:
+        _ctx(c, rr, q, 3, 50)
+    assert e.value.status == 1
