@@ -165,9 +165,10 @@ class DDLPB:
                 self.f[i] += chi_eta(self.t(i, j), self.eta)
         f = self.f
         self.d = np.where(f > 1.0, 1.0 / np.where(f > 1.0, f, 1.0), 1.0)
-        # chi_i^eta = 1 - sum_j omega_ij = 1 - d f
-        self.chi = 1.0 - self.d * f
-        self.chi[np.abs(self.chi) < 1e-300] = 0.0
+        # chi_i^eta = 1 - sum_j omega_ij = 1 - d f, which is exactly 0 where f >= 1
+        # (Sec. 3.1: "if f_n^i > 1 then chi_i^eta(x_i^n) = 0"); written so that no
+        # rounding residue of 1 - (1/f) f survives there
+        self.chi = np.where(f >= 1.0, 0.0, 1.0 - self.d * f)
         self.delta_gt1 = (f > 1.0).astype(np.float64)
         # Z_n^i = sum_{k0 in N_i} chi'(r_1^k0) e^k0 / r_k0
         self.Z = np.zeros((M, N, 3))
