@@ -165,8 +165,8 @@ class DDLPB:
                 self.f[i] += chi_eta(self.t(i, j), self.eta)
         f = self.f
         self.d = np.where(f > 1.0, 1.0 / np.where(f > 1.0, f, 1.0), 1.0)
-        # chi_i^eta = 1 - sum_j omega_ij = 1 - d f, which is exactly 0 where f >= 1
-        # (Sec. 3.1: "if f_n^i > 1 then chi_i^eta(x_i^n) = 0"); written so that no
+        # chi_i^eta = 1 - sum_j omega_ij = 1 - d f, which Sec. 3.1 (below Eq.
+        # derivative_chi_i) notes is exactly zero wherever f > 1; written so that no
         # rounding residue of 1 - (1/f) f survives there
         self.chi = np.where(f >= 1.0, 0.0, 1.0 - self.d * f)
         self.delta_gt1 = (f > 1.0).astype(np.float64)
