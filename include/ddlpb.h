@@ -66,6 +66,8 @@ typedef struct {
     int precision;       /* ddlpb_precision; default DDLPB_FP64 */
     int fmm_order;       /* 0: direct summation of the dense coupling (the only mode of this build) */
     void* cuda_stream;   /* cudaStream_t the context launches on; NULL = legacy default stream */
+    double precond_tol;  /* relative tolerance of the inner A/B solves that apply the L_AB
+                            preconditioner of Sec. 4 inside flexible GMRES; default 1e-3 */
 } ddlpb_options;
 
 typedef struct {
@@ -80,6 +82,7 @@ typedef struct {
     double solve_residual;         /* final FP64 relative residual of the primal solve */
     double adjoint_residual;       /* final FP64 relative residual of the adjoint solve */
     int refinement_steps;          /* FP64 refinement steps of the last solve (mixed precision) */
+    int inner_iterations;          /* inner A/B Krylov iterations of the last solve (preconditioner) */
 } ddlpb_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -112,9 +115,12 @@ DDLPB_API ddlpb_status ddlpb_setup_device(int n, const double* centres, const do
                                 double eps_solvent, double kappa, int lmax, int n_lebedev,
                                 ddlpb_surface surface, const ddlpb_options* opt, ddlpb_ctx** out);
 
-/* Solve L X = g (Eq. AXg) to the relative residual opt.tol.  Warm-starts from the
- * previous solution of this context if there is one.  DDLPB_ENOTCONV if max_iter
- * is reached (X then holds the last iterate). */
+/* Solve L X = g (Eq. AXg) to the FP64 relative residual opt.tol, by flexible GMRES
+ * right-preconditioned with L_AB = diag(A, B) (Sec. 4; the inner A and B solves are
+ * GMRES on the sparse blocks).  In the mixed precision mode the Krylov solve runs in
+ * FP32 inside FP64 iterative refinement.  Warm-starts from the previous solution of
+ * this context if there is one.  DDLPB_ENOTCONV if max_iter is reached (X then holds
+ * the last iterate). */
 DDLPB_API ddlpb_status ddlpb_solve(ddlpb_ctx* ctx);
 
 /* Solve L* X_adj = Q (Eqs. adjoint_system, AstarXg), Q_{j00} = q_j Y_00.  Requires

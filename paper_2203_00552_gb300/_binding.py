@@ -25,14 +25,16 @@ OP_L, OP_LT, OP_AB, OP_ABT, OP_C, OP_CT = range(6)
 
 class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int), ("gmres_restart", C.c_int),
-                ("precision", C.c_int), ("fmm_order", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("precision", C.c_int), ("fmm_order", C.c_int), ("cuda_stream", C.c_void_p),
+                ("precond_tol", C.c_double)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("lmax", C.c_int), ("n_lebedev", C.c_int),
                 ("n_neighbour_pairs", C.c_longlong), ("n_hits", C.c_longlong), ("n_external", C.c_longlong),
                 ("solve_iterations", C.c_int), ("adjoint_iterations", C.c_int), ("solve_residual", C.c_double),
-                ("adjoint_residual", C.c_double), ("refinement_steps", C.c_int)]
+                ("adjoint_residual", C.c_double), ("refinement_steps", C.c_int),
+                ("inner_iterations", C.c_int)]
 
 
 class DDLPBError(RuntimeError):

@@ -25,11 +25,43 @@
 //   Q_l^m     = a[l][m] (z Q_{l-1}^m - b[l][m] Q_{l-2}^m)
 // kr[l] = 1/((2l+1)(2l-1)) drives the scaled k_l recurrence, si[l] the series of
 // the scaled i_l.
-struct YTab {
-    const double* a;     // [DDLPB_LT * DDLPB_LT]
-    const double* b;
-    const double* qmm;   // [DDLPB_LT]
-    const double* q1;    // [DDLPB_LT]
+template <typename T>
+struct YTabT {
+    const T* a;     // [DDLPB_LT * DDLPB_LT]
+    const T* b;
+    const T* qmm;   // [DDLPB_LT]
+    const T* q1;    // [DDLPB_LT]
+};
+using YTab = YTabT<double>;
+
+template <typename T> struct V4T;
+template <> struct V4T<double> { using type = double4; };
+template <> struct V4T<float> { using type = float4; };
+
+// Tables and scratch of the matrix-free operators in one arithmetic type T
+// (double: the FP64 path; float: the inner solves of the mixed-precision form).
+// Positions of the float set are taken relative to the centroid of the solute.
+template <typename T>
+struct OpSet {
+    using V4 = typename V4T<T>::type;
+    bool ready = false;
+    V4* sph = nullptr;      // [M] centre, radius
+    V4* leb = nullptr;      // [N] s_n, w_n
+    T* Y = nullptr;         // [N][nb]
+    T* YT = nullptr;        // [nb][N]
+    T* ytab = nullptr;
+    YTabT<T> yt{};
+    T* Sinv = nullptr;      // [M][lmax+2]
+    T* Khinv = nullptr;     // [M][lmax+2]
+    T* di = nullptr;        // [M][lmax+1]
+    T* cik = nullptr;       // [M][lmax+1]
+    T* hit_w = nullptr;     // [H]
+    T* thit_w = nullptr;    // [H]
+    V4* ext_x = nullptr;    // [E] position, chi
+    T* mu = nullptr;        // [M][nb] scratch
+    T* extA = nullptr;      // [E] scratch
+    T* gridA = nullptr;     // [M*N] scratch
+    T* gridB = nullptr;     // [M*N] scratch
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -50,6 +82,7 @@ struct ddlpb_ctx {
     int device = 0;
     std::string err;
     bool solved = false, adjoint_done = false;
+    bool X_zero = true, Xa_zero = true;   // solution vectors still all zero (skip the first residual matvec)
     ddlpb_info info{};
     std::vector<void*> allocs;
 
@@ -98,12 +131,8 @@ struct ddlpb_ctx {
     double* S0 = nullptr;       // [E] potential of mu0 at external points
 
     // scratch
-    double* gm_V = nullptr;     // Krylov basis [(restart+1)][nvec]
-    double* gm_w = nullptr;     // [nvec]
-    double* gm_r = nullptr;     // [nvec]
-    double* gm_red = nullptr;   // partial reductions
-    double* gm_h = nullptr;     // [restart+2]
-    double* h_pinned = nullptr; // host pinned mirror of gm_h
+    void* solver = nullptr;     // Krylov workspaces (solve.cu)
+    std::vector<void*> pinned;  // pinned host buffers
     double* mu = nullptr;       // [M][nb]
     double* gridA = nullptr;    // [M*N]
     double* gridB = nullptr;    // [M*N]
@@ -112,6 +141,10 @@ struct ddlpb_ctx {
     double* tmpv = nullptr;     // [nvec]
     double* force_acc = nullptr;
     ForceScratch fscr;
+    OpSet<double> d64;          // aliases the double tables above
+    OpSet<float> f32;           // built on first use by the mixed-precision solve
+    double centroid[3] = {0, 0, 0};
+    float* f32_vec = nullptr;   // FP32 Krylov workspace
 };
 
 // ---------------------------------------------------------------------------
@@ -162,7 +195,7 @@ static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) 
 
 // Stream all Y_lm(u), u = (x, y, z) a unit vector, calling f(idx, l, Y).
 template <typename T, typename F>
-__device__ __forceinline__ void ylm_stream(int lmax, T x, T y, T z, const YTab& yt, F&& f) {
+__device__ __forceinline__ void ylm_stream(int lmax, T x, T y, T z, const YTabT<T>& yt, F&& f) {
     const T SQ2 = (T)1.4142135623730951;
     T cr = 1, ci = 0;
     for (int m = 0; m <= lmax; ++m) {
@@ -199,7 +232,7 @@ __device__ __forceinline__ void ylm_stream(int lmax, T x, T y, T z, const YTab& 
 // whose tangential projection G - (u.G) u is the surface gradient of Y_lm at u
 // (used for Eq. derivative_ylm).  Calls f(idx, l, Y, Gx, Gy, Gz).
 template <typename T, typename F>
-__device__ __forceinline__ void ylm_grad_stream(int lmax, T x, T y, T z, const YTab& yt, F&& f) {
+__device__ __forceinline__ void ylm_grad_stream(int lmax, T x, T y, T z, const YTabT<T>& yt, F&& f) {
     const T SQ2 = (T)1.4142135623730951;
     T cr = 1, ci = 0, pr = 0, pi = 0;  // w^m, w^(m-1), w = x + i y
     for (int m = 0; m <= lmax; ++m) {
@@ -346,6 +379,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // ---------------------------------------------------------------------------
 // Host-side internal entry points (defined across the .cu files).
+template <typename T> ddlpb_status opset_prepare(ddlpb_ctx* c, OpSet<T>& S);
+template <typename T> ddlpb_status op_apply_L_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose);
+template <typename T>
+ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE);
 ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const double* radii,
                                   const double* charges, bool device_ptrs, int surface);
 ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose);
@@ -362,3 +399,4 @@ ddlpb_status op_source_multipoles(ddlpb_ctx* c, const double* x, double* mu);
 ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double* x, int* iters,
                           double* resid);
 ddlpb_status compute_forces(ddlpb_ctx* c, double* f_dev);
+void solver_state_free(ddlpb_ctx* c);

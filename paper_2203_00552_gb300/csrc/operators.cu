@@ -1,5 +1,5 @@
 // operators.cu -- the operators of the ddLPB system L X = g (Eq. AXg) and its adjoint
-// L* (Eq. AstarXg), applied matrix-free on the device.
+// L* (Eq. AstarXg), applied matrix-free on the device, in FP64 or FP32.
 //
 //   A, B  (Eqs. definition_of_A_matrix, definition_of_B_matrix): identity minus the
 //         projection onto Y_lm(s_n) of the neighbour expansions, weighted by
@@ -12,18 +12,21 @@
 #include "common.cuh"
 
 #define BLK 128
+#define YK_TS 8
 
 // ---------------------------------------------------------------- projections
 
 // grid[row][n] = (w_n if weighted) * sum_lm YT[lm][n] coef[row][lm]
-__global__ void k_synthesis(int N, int nb, const double* __restrict__ YT, const double4* __restrict__ leb,
-                            const double* __restrict__ coef, double* __restrict__ grid, int weighted) {
-    extern __shared__ double sc[];
+template <typename T, typename V4>
+__global__ void k_synthesis(int N, int nb, const T* __restrict__ YT, const V4* __restrict__ leb,
+                            const T* __restrict__ coef, T* __restrict__ grid, int weighted) {
+    extern __shared__ unsigned char smraw[];
+    T* sc = (T*)smraw;
     int row = blockIdx.x;
     for (int k = threadIdx.x; k < nb; k += blockDim.x) sc[k] = coef[(size_t)row * nb + k];
     __syncthreads();
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        double v = 0;
+        T v = 0;
         for (int k = 0; k < nb; ++k) v += YT[(size_t)k * N + n] * sc[k];
         if (weighted) v *= leb[n].w;
         grid[(size_t)row * N + n] = v;
@@ -31,15 +34,15 @@ __global__ void k_synthesis(int N, int nb, const double* __restrict__ YT, const 
 }
 
 // out[i][lm] (+)= scale * (cik[i][l]) * sum_{external t of i} w_n chi_t val[t] Y_lm(s_n)
+template <typename T, typename V4>
 __global__ void k_masked_analysis(int N, int nb, int L, const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
-                                  const double4* __restrict__ ext_x, const double4* __restrict__ leb,
-                                  const double* __restrict__ Y, const double* __restrict__ val, double scale,
-                                  const double* __restrict__ cik, double* __restrict__ out, int out_stride,
-                                  int accumulate) {
-    extern __shared__ double sm[];
+                                  const V4* __restrict__ ext_x, const V4* __restrict__ leb,
+                                  const T* __restrict__ Y, const T* __restrict__ val, T scale,
+                                  const T* __restrict__ cik, T* __restrict__ out, int out_stride, int accumulate) {
+    extern __shared__ unsigned char smraw[];
     int i = blockIdx.x;
     int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
-    double* gv = sm;
+    T* gv = (T*)smraw;
     int* gn = (int*)(gv + N);
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         int t = t0 + k;
@@ -49,12 +52,12 @@ __global__ void k_masked_analysis(int N, int nb, int L, const int* __restrict__ 
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        double a = 0;
+        T a = 0;
         for (int k = 0; k < cnt; ++k) a += Y[(size_t)gn[k] * nb + idx] * gv[k];
         int l = (int)sqrtf((float)idx + 0.5f);
         if (cik) a *= cik[(size_t)i * (L + 1) + l];
         a *= scale;
-        double* o = out + (size_t)i * out_stride + idx;
+        T* o = out + (size_t)i * out_stride + idx;
         *o = accumulate ? *o + a : a;
     }
 }
@@ -64,38 +67,40 @@ __global__ void k_masked_analysis(int N, int nb, int L, const int* __restrict__ 
 // One CTA per sphere i.  For every grid point n the neighbour expansions of X_r
 // (basis r_l^j Y^j) and X_e (basis i-ratio Y^j) are summed with omega_ij^eta; the
 // grid values are projected back and subtracted from the identity.
-__global__ void k_ab_apply(int M, int N, int nb, int L, double kappa, const double4* __restrict__ sph,
-                           const double4* __restrict__ leb, YTab yt, const int* __restrict__ hptr,
-                           const int* __restrict__ hj, const double* __restrict__ hw, const double* __restrict__ Sinv,
-                           const double* __restrict__ Y, const double* __restrict__ x, double* __restrict__ y,
-                           double* __restrict__ gridR, double* __restrict__ gridE) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_ab_apply(int M, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
+                           const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ hptr,
+                           const int* __restrict__ hj, const T* __restrict__ hw, const T* __restrict__ Sinv,
+                           const T* __restrict__ Y, const T* __restrict__ x, T* __restrict__ y,
+                           T* __restrict__ gridR, T* __restrict__ gridE) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x;
-    double* vr = sm;
-    double* ve = vr + N;
-    double* rr = ve + N;
-    double* ri = rr + (L + 1) * bd;
+    T* vr = sm;
+    T* ve = vr + N;
+    T* rr = ve + N;
+    T* ri = rr + (L + 1) * bd;
     const int i = blockIdx.x;
-    const double4 a = sph[i];
-    const double* xr = x;
-    const double* xe = x + (size_t)M * nb;
+    const V4 a = sph[i];
+    const T* xr = x;
+    const T* xe = x + (size_t)M * nb;
     for (int n = tid; n < N; n += bd) {
-        double4 s = leb[n];
-        double px = a.x + a.w * s.x, py = a.y + a.w * s.y, pz = a.z + a.w * s.z;
+        V4 s = leb[n];
+        T px = a.x + a.w * s.x, py = a.y + a.w * s.y, pz = a.z + a.w * s.z;
         long long p = (long long)i * N + n;
-        double sr = 0, se = 0;
+        T sr = 0, se = 0;
         for (int h = hptr[p]; h < hptr[p + 1]; ++h) {
             int j = hj[h];
-            double w = hw[h];
-            double4 b = sph[j];
-            double dx = px - b.x, dy = py - b.y, dz = pz - b.z;
-            double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
-            radial<double>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
-            radial<double>(1, L, rho, b.w, kappa, Sinv + (size_t)j * (L + 2), ri + tid, nullptr, bd);
-            const double* Xr = xr + (size_t)j * nb;
-            const double* Xe = xe + (size_t)j * nb;
-            double ur = 0, ue = 0;
-            ylm_stream<double>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, double yv) {
+            T w = hw[h];
+            V4 b = sph[j];
+            T dx = px - b.x, dy = py - b.y, dz = pz - b.z;
+            T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
+            radial<T>(1, L, rho, b.w, kappa, Sinv + (size_t)j * (L + 2), ri + tid, nullptr, bd);
+            const T* Xr = xr + (size_t)j * nb;
+            const T* Xe = xe + (size_t)j * nb;
+            T ur = 0, ue = 0;
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
                 ur += __ldg(Xr + idx) * rr[tid + l * bd] * yv;
                 ue += __ldg(Xe + idx) * ri[tid + l * bd] * yv;
             });
@@ -112,9 +117,9 @@ __global__ void k_ab_apply(int M, int N, int nb, int L, double kappa, const doub
     __syncthreads();
     if (!y) return;
     for (int idx = tid; idx < nb; idx += bd) {
-        double ar = 0, ae = 0;
+        T ar = 0, ae = 0;
         for (int n = 0; n < N; ++n) {
-            double wy = leb[n].w * Y[(size_t)n * nb + idx];
+            T wy = leb[n].w * Y[(size_t)n * nb + idx];
             ar += wy * vr[n];
             ae += wy * ve[n];
         }
@@ -126,43 +131,45 @@ __global__ void k_ab_apply(int M, int N, int nb, int L, double kappa, const doub
 
 // A^T and B^T: one CTA per sphere j gathers every hit (i, n) -> j.
 // zr, ze are the weighted syntheses w_n sum_lm Y_lm(s_n) x_{i lm} of the two blocks.
-__global__ void k_ab_transpose(int M, int N, int nb, int L, double kappa, const double4* __restrict__ sph,
-                               const double4* __restrict__ leb, YTab yt, const int* __restrict__ tptr,
-                               const int* __restrict__ tp, const double* __restrict__ tw,
-                               const double* __restrict__ Sinv, const double* __restrict__ zr,
-                               const double* __restrict__ ze, const double* __restrict__ x, double* __restrict__ y) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
+                               const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ tptr,
+                               const int* __restrict__ tp, const T* __restrict__ tw, const T* __restrict__ Sinv,
+                               const T* __restrict__ zr, const T* __restrict__ ze, const T* __restrict__ x,
+                               T* __restrict__ y) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-    double* accR = sm;
-    double* accE = accR + nw * nb;
-    double* rr = accE + nw * nb;
-    double* ri = rr + (L + 1) * bd;
+    T* accR = sm;
+    T* accE = accR + nw * nb;
+    T* rr = accE + nw * nb;
+    T* ri = rr + (L + 1) * bd;
     const int j = blockIdx.x;
-    const double4 b = sph[j];
+    const V4 b = sph[j];
     for (int k = tid; k < 2 * nw * nb; k += bd) sm[k] = 0;
     __syncthreads();
     const int t0 = tptr[j], cnt = tptr[j + 1] - t0;
-    const double* sinv = Sinv + (size_t)j * (L + 2);
+    const T* sinv = Sinv + (size_t)j * (L + 2);
     for (int base = 0; base < cnt; base += bd) {
         int h = base + tid;
-        double dx = b.w, dy = 0, dz = 0, wr = 0, we = 0;
+        T dx = b.w, dy = 0, dz = 0, wr = 0, we = 0;
         if (h < cnt) {
             int p = tp[t0 + h];
             int i = p / N, n = p % N;
-            double4 a = sph[i], s = leb[n];
+            V4 a = sph[i], s = leb[n];
             dx = a.x + a.w * s.x - b.x;
             dy = a.y + a.w * s.y - b.y;
             dz = a.z + a.w * s.z - b.z;
-            double w = tw[t0 + h];
+            T w = tw[t0 + h];
             wr = w * zr[p];
             we = w * ze[p];
         }
-        double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
-        radial<double>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
-        radial<double>(1, L, rho, b.w, kappa, sinv, ri + tid, nullptr, bd);
-        ylm_stream<double>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, double yv) {
-            double vR = warp_sum(wr * rr[tid + l * bd] * yv);
-            double vE = warp_sum(we * ri[tid + l * bd] * yv);
+        T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+        radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
+        radial<T>(1, L, rho, b.w, kappa, sinv, ri + tid, nullptr, bd);
+        ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
+            T vR = warp_sum(wr * rr[tid + l * bd] * yv);
+            T vE = warp_sum(we * ri[tid + l * bd] * yv);
             if (lane == 0) {
                 accR[warp * nb + idx] += vR;
                 accE[warp * nb + idx] += vE;
@@ -171,7 +178,7 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, double kappa, const 
     }
     __syncthreads();
     for (int idx = tid; idx < nb; idx += bd) {
-        double sr = 0, se = 0;
+        T sr = 0, se = 0;
         for (int w = 0; w < nw; ++w) {
             sr += accR[w * nb + idx];
             se += accE[w * nb + idx];
@@ -185,35 +192,34 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, double kappa, const 
 // ---------------------------------------------------------------- dense coupling (L_C)
 
 // mu_j = C_ik^j * P chi_j y_j with y_j = eps1/eps2 (l/r_j) X_r,j - i_l'/i_l X_e,j, for j in src.
-__global__ void k_source_mu(int M, int N, int nb, int L, double e12, const int* __restrict__ src,
-                            const double4* __restrict__ sph, const double* __restrict__ di,
-                            const double* __restrict__ cik, const int* __restrict__ ext_ptr,
-                            const int* __restrict__ ext_p, const double4* __restrict__ ext_x,
-                            const double4* __restrict__ leb, const double* __restrict__ Y,
-                            const double* __restrict__ x, double* __restrict__ mu) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_source_mu(int M, int N, int nb, int L, T e12, const int* __restrict__ src,
+                            const V4* __restrict__ sph, const T* __restrict__ di, const T* __restrict__ cik,
+                            const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
+                            const V4* __restrict__ ext_x, const V4* __restrict__ leb, const T* __restrict__ Y,
+                            const T* __restrict__ x, T* __restrict__ mu) {
+    extern __shared__ unsigned char smraw[];
     const int j = src[blockIdx.x];
-    double* yv = sm;
-    double* gv = yv + nb;
+    T* yv = (T*)smraw;
+    T* gv = yv + nb;
     int* gn = (int*)(gv + N);
-    const double rj = sph[j].w;
+    const T rj = sph[j].w;
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
         int l = (int)sqrtf((float)idx + 0.5f);
-        yv[idx] = e12 * (double)l / rj * x[(size_t)j * nb + idx] -
-                  di[(size_t)j * (L + 1) + l] * x[(size_t)(M + j) * nb + idx];
+        yv[idx] = e12 * (T)l / rj * x[(size_t)j * nb + idx] - di[(size_t)j * (L + 1) + l] * x[(size_t)(M + j) * nb + idx];
     }
     __syncthreads();
     const int t0 = ext_ptr[j], cnt = ext_ptr[j + 1] - t0;
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         int t = t0 + k, n = ext_p[t] % N;
-        double v = 0;
+        T v = 0;
         for (int idx = 0; idx < nb; ++idx) v += Y[(size_t)n * nb + idx] * yv[idx];
         gn[k] = n;
         gv[k] = leb[n].w * ext_x[t].w * v;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        double a = 0;
+        T a = 0;
         for (int k = 0; k < cnt; ++k) a += Y[(size_t)gn[k] * nb + idx] * gv[k];
         int l = (int)sqrtf((float)idx + 0.5f);
         mu[(size_t)j * nb + idx] = cik[(size_t)j * (L + 1) + l] * a;
@@ -223,21 +229,22 @@ __global__ void k_source_mu(int M, int N, int nb, int L, double e12, const int* 
 // phi(x_t) = sum_{j in src} sum_lm mu_j,lm k_l^j(x_t) Y_lm^j(x_t) at every external point t
 // (the potential in Eqs. definition_of_Q_matrix / defintion_of_S).  Direct summation: one
 // thread per target, source tiles staged in shared memory.
-#define YK_TS 8
-__global__ void k_yukawa_pot(int E, const double4* __restrict__ ext_x, int n_src, const int* __restrict__ src,
-                             const double4* __restrict__ sph, const double* __restrict__ mu,
-                             const double* __restrict__ Khinv, int nb, int L, double kappa, YTab yt,
-                             double* __restrict__ phi) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_yukawa_pot(int E, const V4* __restrict__ ext_x, int n_src, const int* __restrict__ src,
+                             const V4* __restrict__ sph, const T* __restrict__ mu, const T* __restrict__ Khinv,
+                             int nb, int L, T kappa, YTabT<T> yt, T* __restrict__ phi) {
+    extern __shared__ unsigned char smraw[];
     const int bd = blockDim.x, tid = threadIdx.x;
-    double4* sp = (double4*)sm;
-    double* smu = (double*)(sp + YK_TS);
-    double* skh = smu + YK_TS * nb;
-    double* rad = skh + YK_TS * (L + 2);
+    V4* sp = (V4*)smraw;
+    T* smu = (T*)(sp + YK_TS);
+    T* skh = smu + YK_TS * nb;
+    T* rad = skh + YK_TS * (L + 2);
     const int t = blockIdx.x * bd + tid;
     const bool valid = t < E;
-    const double4 xt = valid ? ext_x[t] : make_double4(0, 0, 0, 0);
-    double acc = 0;
+    V4 xt;
+    if (valid) xt = ext_x[t];
+    else xt.x = xt.y = xt.z = xt.w = 0;
+    T acc = 0;
     for (int base = 0; base < n_src; base += YK_TS) {
         int ns = min(YK_TS, n_src - base);
         __syncthreads();
@@ -252,14 +259,14 @@ __global__ void k_yukawa_pot(int E, const double4* __restrict__ ext_x, int n_src
         if (tid < ns) sp[tid] = sph[src[base + tid]];
         __syncthreads();
         for (int s = 0; s < ns; ++s) {
-            double4 b = sp[s];
-            double dx = valid ? xt.x - b.x : b.w, dy = valid ? xt.y - b.y : 0, dz = valid ? xt.z - b.z : 0;
-            double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
-            radial<double>(2, L, rho, b.w, kappa, skh + s * (L + 2), rad + tid, nullptr, bd);
-            const double* m = smu + s * nb;
-            double v = 0;
-            ylm_stream<double>(L, dx * inv, dy * inv, dz * inv, yt,
-                               [&](int idx, int l, double yv) { v += m[idx] * rad[tid + l * bd] * yv; });
+            V4 b = sp[s];
+            T dx = valid ? xt.x - b.x : b.w, dy = valid ? xt.y - b.y : (T)0, dz = valid ? xt.z - b.z : (T)0;
+            T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(2, L, rho, b.w, kappa, skh + s * (L + 2), rad + tid, nullptr, bd);
+            const T* m = smu + s * nb;
+            T v = 0;
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
+                          [&](int idx, int l, T yv) { v += m[idx] * rad[tid + l * bd] * yv; });
             acc += v;
         }
     }
@@ -267,50 +274,52 @@ __global__ void k_yukawa_pot(int E, const double4* __restrict__ ext_x, int n_src
 }
 
 // nu_j = sum_t c_t k_l^j(x_t) Y_lm^j(x_t) (transpose of k_yukawa_pot), one CTA per source j.
-__global__ void k_yukawa_adj(int E, const double4* __restrict__ ext_x, const double* __restrict__ cext,
-                             const int* __restrict__ src, const double4* __restrict__ sph,
-                             const double* __restrict__ Khinv, int nb, int L, double kappa, YTab yt,
-                             double* __restrict__ nu) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_yukawa_adj(int E, const V4* __restrict__ ext_x, const T* __restrict__ cext,
+                             const int* __restrict__ src, const V4* __restrict__ sph, const T* __restrict__ Khinv,
+                             int nb, int L, T kappa, YTabT<T> yt, T* __restrict__ nu) {
+    extern __shared__ unsigned char smraw[];
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-    double* acc = sm;
-    double* kh = acc + nw * nb;
-    double* rad = kh + (L + 2);
+    T* acc = (T*)smraw;
+    T* kh = acc + nw * nb;
+    T* rad = kh + (L + 2);
     const int j = src[blockIdx.x];
-    const double4 b = sph[j];
+    const V4 b = sph[j];
     for (int k = tid; k < nw * nb; k += bd) acc[k] = 0;
     for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
     __syncthreads();
     for (int base = 0; base < E; base += bd) {
         int t = base + tid;
-        double dx = b.w, dy = 0, dz = 0, c = 0;
+        T dx = b.w, dy = 0, dz = 0, c = 0;
         if (t < E) {
-            double4 xt = ext_x[t];
+            V4 xt = ext_x[t];
             dx = xt.x - b.x;
             dy = xt.y - b.y;
             dz = xt.z - b.z;
             c = cext[t];
         }
-        double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
-        radial<double>(2, L, rho, b.w, kappa, kh, rad + tid, nullptr, bd);
-        ylm_stream<double>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, double yv) {
-            double v = warp_sum(c * rad[tid + l * bd] * yv);
+        T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+        radial<T>(2, L, rho, b.w, kappa, kh, rad + tid, nullptr, bd);
+        ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
+            T v = warp_sum(c * rad[tid + l * bd] * yv);
             if (lane == 0) acc[warp * nb + idx] += v;
         });
     }
     __syncthreads();
     for (int idx = tid; idx < nb; idx += bd) {
-        double s = 0;
+        T s = 0;
         for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
         nu[(size_t)j * nb + idx] = s;
     }
 }
 
 // c_t = w_n chi_t sum_lm Y_lm(s_n) (x_r + x_e)_{i lm} at the external points of sphere i.
+template <typename T, typename V4>
 __global__ void k_ext_weights(int M, int N, int nb, const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
-                              const double4* __restrict__ ext_x, const double4* __restrict__ leb,
-                              const double* __restrict__ Y, const double* __restrict__ x, double* __restrict__ cext) {
-    extern __shared__ double sm[];
+                              const V4* __restrict__ ext_x, const V4* __restrict__ leb, const T* __restrict__ Y,
+                              const T* __restrict__ x, T* __restrict__ cext) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
     const int i = blockIdx.x;
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x)
         sm[idx] = x[(size_t)i * nb + idx] + x[(size_t)(M + i) * nb + idx];
@@ -318,23 +327,23 @@ __global__ void k_ext_weights(int M, int N, int nb, const int* __restrict__ ext_
     const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         int t = t0 + k, n = ext_p[t] % N;
-        double v = 0;
+        T v = 0;
         for (int idx = 0; idx < nb; ++idx) v += Y[(size_t)n * nb + idx] * sm[idx];
         cext[t] = leb[n].w * ext_x[t].w * v;
     }
 }
 
 // y_r,j += eps1/eps2 (l/r_j) z_j, y_e,j += -i_l'/i_l z_j with z_j = P chi_j (C_ik nu_j).
-__global__ void k_ct_finish(int M, int N, int nb, int L, double e12, const int* __restrict__ src,
-                            const double4* __restrict__ sph, const double* __restrict__ di,
-                            const double* __restrict__ cik, const int* __restrict__ ext_ptr,
-                            const int* __restrict__ ext_p, const double4* __restrict__ ext_x,
-                            const double4* __restrict__ leb, const double* __restrict__ Y,
-                            const double* __restrict__ nu, double* __restrict__ y) {
-    extern __shared__ double sm[];
+template <typename T, typename V4>
+__global__ void k_ct_finish(int M, int N, int nb, int L, T e12, const int* __restrict__ src,
+                            const V4* __restrict__ sph, const T* __restrict__ di, const T* __restrict__ cik,
+                            const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
+                            const V4* __restrict__ ext_x, const V4* __restrict__ leb, const T* __restrict__ Y,
+                            const T* __restrict__ nu, T* __restrict__ y) {
+    extern __shared__ unsigned char smraw[];
     const int j = src[blockIdx.x];
-    double* u = sm;
-    double* gv = u + nb;
+    T* u = (T*)smraw;
+    T* gv = u + nb;
     int* gn = (int*)(gv + N);
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
         int l = (int)sqrtf((float)idx + 0.5f);
@@ -344,19 +353,44 @@ __global__ void k_ct_finish(int M, int N, int nb, int L, double e12, const int* 
     const int t0 = ext_ptr[j], cnt = ext_ptr[j + 1] - t0;
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         int t = t0 + k, n = ext_p[t] % N;
-        double v = 0;
+        T v = 0;
         for (int idx = 0; idx < nb; ++idx) v += Y[(size_t)n * nb + idx] * u[idx];
         gn[k] = n;
         gv[k] = leb[n].w * ext_x[t].w * v;
     }
     __syncthreads();
-    const double rj = sph[j].w;
+    const T rj = sph[j].w;
     for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-        double a = 0;
+        T a = 0;
         for (int k = 0; k < cnt; ++k) a += Y[(size_t)gn[k] * nb + idx] * gv[k];
         int l = (int)sqrtf((float)idx + 0.5f);
-        y[(size_t)j * nb + idx] += e12 * (double)l / rj * a;
+        y[(size_t)j * nb + idx] += e12 * (T)l / rj * a;
         y[(size_t)(M + j) * nb + idx] += -di[(size_t)j * (L + 1) + l] * a;
+    }
+}
+
+// ---------------------------------------------------------------- FP32 tables
+
+template <typename S, typename D>
+__global__ void k_convert(long long n, const S* __restrict__ a, D* __restrict__ b) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) b[k] = (D)a[k];
+}
+
+__global__ void k_convert_pos(int n, const double4* __restrict__ a, float4* __restrict__ b, double cx, double cy,
+                              double cz) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        double4 v = a[k];
+        b[k] = make_float4((float)(v.x - cx), (float)(v.y - cy), (float)(v.z - cz), (float)v.w);
+    }
+}
+
+__global__ void k_convert_leb(int n, const double4* __restrict__ a, float4* __restrict__ b) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        double4 v = a[k];
+        b[k] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
     }
 }
 
@@ -367,107 +401,247 @@ static ddlpb_status set_smem(ddlpb_ctx* c, const void* fn, size_t bytes) {
     return DDLPB_OK;
 }
 
-ddlpb_status op_synthesis(ddlpb_ctx* c, const double* coef, int rows, double* grid, bool weighted) {
+template <typename S, typename D>
+static ddlpb_status convert(ddlpb_ctx* c, const S* a, D** b, long long n) {
+    DDLPB_TRY(ctx_alloc(c, b, n));
+    if (n > 0) {
+        k_convert<S, D><<<ceil_div(n, 256), 256, 0, c->stream>>>(n, a, *b);
+        DDLPB_LAUNCHED(c, "convert");
+    }
+    return DDLPB_OK;
+}
+
+template <>
+ddlpb_status opset_prepare<double>(ddlpb_ctx* c, OpSet<double>& S) {
+    if (S.ready) return DDLPB_OK;
+    S.sph = c->sph;
+    S.leb = c->leb;
+    S.Y = c->Y;
+    S.YT = c->YT;
+    S.ytab = c->ytab;
+    S.yt = c->yt;
+    S.Sinv = c->Sinv;
+    S.Khinv = c->Khinv;
+    S.di = c->di;
+    S.cik = c->cik;
+    S.hit_w = c->hit_w;
+    S.thit_w = c->thit_w;
+    S.ext_x = c->ext_x;
+    S.mu = c->mu;
+    S.extA = c->extA;
+    S.gridA = c->gridA;
+    S.gridB = c->gridB;
+    S.ready = true;
+    return DDLPB_OK;
+}
+
+template <>
+ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
+    if (S.ready) return DDLPB_OK;
+    const int M = c->M, N = c->N, nb = c->nb, L = c->lmax;
+    const long long MN = (long long)M * N;
+    DDLPB_TRY(ctx_alloc(c, &S.sph, M));
+    k_convert_pos<<<ceil_div(M, 256), 256, 0, c->stream>>>(M, c->sph, S.sph, c->centroid[0], c->centroid[1],
+                                                           c->centroid[2]);
+    DDLPB_LAUNCHED(c, "convert_pos");
+    DDLPB_TRY(ctx_alloc(c, &S.leb, N));
+    k_convert_leb<<<ceil_div(N, 256), 256, 0, c->stream>>>(N, c->leb, S.leb);
+    DDLPB_LAUNCHED(c, "convert_leb");
+    DDLPB_TRY(ctx_alloc(c, &S.ext_x, c->E));
+    if (c->E > 0) {
+        k_convert_pos<<<ceil_div(c->E, 256), 256, 0, c->stream>>>(c->E, c->ext_x, S.ext_x, c->centroid[0],
+                                                                  c->centroid[1], c->centroid[2]);
+        DDLPB_LAUNCHED(c, "convert_ext");
+    }
+    const long long ntab = 2LL * DDLPB_LT * DDLPB_LT + 2 * DDLPB_LT;
+    DDLPB_TRY(convert(c, c->ytab, &S.ytab, ntab));
+    S.yt.a = S.ytab;
+    S.yt.b = S.ytab + DDLPB_LT * DDLPB_LT;
+    S.yt.qmm = S.yt.b + DDLPB_LT * DDLPB_LT;
+    S.yt.q1 = S.yt.qmm + DDLPB_LT;
+    DDLPB_TRY(convert(c, c->Y, &S.Y, (long long)N * nb));
+    DDLPB_TRY(convert(c, c->YT, &S.YT, (long long)N * nb));
+    DDLPB_TRY(convert(c, c->Sinv, &S.Sinv, (long long)M * (L + 2)));
+    DDLPB_TRY(convert(c, c->Khinv, &S.Khinv, (long long)M * (L + 2)));
+    DDLPB_TRY(convert(c, c->di, &S.di, (long long)M * (L + 1)));
+    DDLPB_TRY(convert(c, c->cik, &S.cik, (long long)M * (L + 1)));
+    DDLPB_TRY(convert(c, c->hit_w, &S.hit_w, c->H));
+    DDLPB_TRY(convert(c, c->thit_w, &S.thit_w, c->H));
+    DDLPB_TRY(ctx_alloc(c, &S.mu, (size_t)M * nb));
+    DDLPB_TRY(ctx_alloc(c, &S.extA, c->E));
+    DDLPB_TRY(ctx_alloc(c, &S.gridA, MN));
+    DDLPB_TRY(ctx_alloc(c, &S.gridB, MN));
+    DDLPB_CK(c, cudaMemsetAsync(S.mu, 0, sizeof(float) * M * nb, c->stream));
+    S.ready = true;
+    return DDLPB_OK;
+}
+
+template <typename T>
+static ddlpb_status synthesis_T(ddlpb_ctx* c, OpSet<T>& S, const T* coef, int rows, T* grid, bool weighted) {
     if (rows <= 0) return DDLPB_OK;
-    k_synthesis<<<rows, BLK, sizeof(double) * c->nb, c->stream>>>(c->N, c->nb, c->YT, c->leb, coef, grid, weighted);
+    k_synthesis<T><<<rows, BLK, sizeof(T) * c->nb, c->stream>>>(c->N, c->nb, S.YT, S.leb, coef, grid, weighted);
     DDLPB_LAUNCHED(c, "synthesis");
     return DDLPB_OK;
 }
 
-ddlpb_status op_masked_analysis(ddlpb_ctx* c, const double* val_ext, double scale, const double* cik_scale,
-                                double* out, int out_stride, int accumulate) {
-    size_t smem = (sizeof(double) + sizeof(int)) * c->N;
-    k_masked_analysis<<<c->M, BLK, smem, c->stream>>>(c->N, c->nb, c->lmax, c->ext_ptr, c->ext_p, c->ext_x, c->leb,
-                                                      c->Y, val_ext, scale, cik_scale, out, out_stride, accumulate);
+template <typename T>
+static ddlpb_status masked_analysis_T(ddlpb_ctx* c, OpSet<T>& S, const T* val_ext, T scale, const T* cik_scale,
+                                      T* out, int out_stride, int accumulate) {
+    size_t smem = (sizeof(T) + sizeof(int)) * c->N;
+    k_masked_analysis<T><<<c->M, BLK, smem, c->stream>>>(c->N, c->nb, c->lmax, c->ext_ptr, c->ext_p, S.ext_x, S.leb,
+                                                         S.Y, val_ext, scale, cik_scale, out, out_stride, accumulate);
     DDLPB_LAUNCHED(c, "masked_analysis");
     return DDLPB_OK;
 }
 
-ddlpb_status op_apply_AB(ddlpb_ctx* c, const double* x, double* y, bool transpose, double* gridR, double* gridE) {
+template <typename T>
+ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE) {
+    DDLPB_TRY(opset_prepare<T>(c, S));
     const int L = c->lmax;
     if (!transpose) {
-        size_t smem = sizeof(double) * (2 * (size_t)c->N + 2 * (size_t)(L + 1) * BLK);
-        DDLPB_TRY(set_smem(c, (const void*)k_ab_apply, smem));
-        k_ab_apply<<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, c->kappa, c->sph, c->leb, c->yt, c->hit_ptr,
-                                                   c->hit_j, c->hit_w, c->Sinv, c->Y, x, y, gridR, gridE);
+        size_t smem = sizeof(T) * (2 * (size_t)c->N + 2 * (size_t)(L + 1) * BLK);
+        DDLPB_TRY(set_smem(c, (const void*)k_ab_apply<T, typename OpSet<T>::V4>, smem));
+        k_ab_apply<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
+                                                      c->hit_ptr, c->hit_j, S.hit_w, S.Sinv, S.Y, x, y, gridR, gridE);
         DDLPB_LAUNCHED(c, "ab_apply");
         return DDLPB_OK;
     }
-    // weighted syntheses of both blocks into gridA (X_r rows) and gridB (X_e rows)
-    DDLPB_TRY(op_synthesis(c, x, c->M, c->gridA, true));
-    DDLPB_TRY(op_synthesis(c, x + (size_t)c->M * c->nb, c->M, c->gridB, true));
-    size_t smem = sizeof(double) * (2 * (size_t)(BLK / 32) * c->nb + 2 * (size_t)(L + 1) * BLK);
-    DDLPB_TRY(set_smem(c, (const void*)k_ab_transpose, smem));
-    k_ab_transpose<<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, c->kappa, c->sph, c->leb, c->yt, c->thit_ptr,
-                                                   c->thit_p, c->thit_w, c->Sinv, c->gridA, c->gridB, x, y);
+    DDLPB_TRY(synthesis_T<T>(c, S, x, c->M, S.gridA, true));
+    DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
+    size_t smem = sizeof(T) * (2 * (size_t)(BLK / 32) * c->nb + 2 * (size_t)(L + 1) * BLK);
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_transpose<T, typename OpSet<T>::V4>, smem));
+    k_ab_transpose<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
+                                                      c->thit_ptr, c->thit_p, S.thit_w, S.Sinv, S.gridA, S.gridB, x,
+                                                      y);
     DDLPB_LAUNCHED(c, "ab_transpose");
     return DDLPB_OK;
 }
 
-ddlpb_status op_source_multipoles(ddlpb_ctx* c, const double* x, double* mu) {
+template <typename T>
+static ddlpb_status source_mu_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* mu) {
     if (c->n_src == 0) return DDLPB_OK;
-    size_t smem = sizeof(double) * (c->nb + c->N) + sizeof(int) * c->N;
-    k_source_mu<<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, c->eps1 / c->eps2, c->src, c->sph,
-                                                    c->di, c->cik, c->ext_ptr, c->ext_p, c->ext_x, c->leb, c->Y, x,
-                                                    mu);
+    size_t smem = sizeof(T) * (c->nb + c->N) + sizeof(int) * c->N;
+    k_source_mu<T><<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, (T)(c->eps1 / c->eps2), c->src,
+                                                       S.sph, S.di, S.cik, c->ext_ptr, c->ext_p, S.ext_x, S.leb, S.Y,
+                                                       x, mu);
     DDLPB_LAUNCHED(c, "source_mu");
     return DDLPB_OK;
 }
 
-ddlpb_status op_yukawa_potential(ddlpb_ctx* c, const double* mu, double* phi_ext) {
+template <typename T>
+static ddlpb_status yukawa_pot_T(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     if (c->E == 0) return DDLPB_OK;
     const int L = c->lmax;
-    size_t smem = sizeof(double4) * YK_TS + sizeof(double) * (YK_TS * (size_t)c->nb + YK_TS * (size_t)(L + 2) +
-                                                              (size_t)(L + 1) * BLK);
-    DDLPB_TRY(set_smem(c, (const void*)k_yukawa_pot, smem));
-    k_yukawa_pot<<<ceil_div(c->E, BLK), BLK, smem, c->stream>>>(c->E, c->ext_x, c->n_src, c->src, c->sph, mu,
-                                                                c->Khinv, c->nb, L, c->kappa, c->yt, phi_ext);
+    using V4 = typename OpSet<T>::V4;
+    size_t smem = sizeof(V4) * YK_TS + sizeof(T) * (YK_TS * (size_t)c->nb + YK_TS * (size_t)(L + 2) +
+                                                     (size_t)(L + 1) * BLK);
+    DDLPB_TRY(set_smem(c, (const void*)k_yukawa_pot<T, V4>, smem));
+    k_yukawa_pot<T><<<ceil_div(c->E, BLK), BLK, smem, c->stream>>>(c->E, S.ext_x, c->n_src, c->src, S.sph, mu,
+                                                                   S.Khinv, c->nb, L, (T)c->kappa, S.yt, phi_ext);
     DDLPB_LAUNCHED(c, "yukawa_pot");
     return DDLPB_OK;
 }
 
-ddlpb_status op_yukawa_adjoint(ddlpb_ctx* c, const double* c_ext, double* nu) {
+template <typename T>
+static ddlpb_status yukawa_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
     if (c->n_src == 0) return DDLPB_OK;
     const int L = c->lmax;
-    size_t smem = sizeof(double) * ((size_t)(BLK / 32) * c->nb + (L + 2) + (size_t)(L + 1) * BLK);
-    DDLPB_TRY(set_smem(c, (const void*)k_yukawa_adj, smem));
-    k_yukawa_adj<<<c->n_src, BLK, smem, c->stream>>>(c->E, c->ext_x, c_ext, c->src, c->sph, c->Khinv, c->nb, L,
-                                                     c->kappa, c->yt, nu);
+    using V4 = typename OpSet<T>::V4;
+    size_t smem = sizeof(T) * ((size_t)(BLK / 32) * c->nb + (L + 2) + (size_t)(L + 1) * BLK);
+    DDLPB_TRY(set_smem(c, (const void*)k_yukawa_adj<T, V4>, smem));
+    k_yukawa_adj<T><<<c->n_src, BLK, smem, c->stream>>>(c->E, S.ext_x, c_ext, c->src, S.sph, S.Khinv, c->nb, L,
+                                                        (T)c->kappa, S.yt, nu);
     DDLPB_LAUNCHED(c, "yukawa_adj");
     return DDLPB_OK;
 }
 
-ddlpb_status op_ext_weights(ddlpb_ctx* c, const double* x, double* cext) {
-    k_ext_weights<<<c->M, BLK, sizeof(double) * c->nb, c->stream>>>(c->M, c->N, c->nb, c->ext_ptr, c->ext_p, c->ext_x,
-                                                                    c->leb, c->Y, x, cext);
+template <typename T>
+static ddlpb_status ext_weights_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* cext) {
+    k_ext_weights<T><<<c->M, BLK, sizeof(T) * c->nb, c->stream>>>(c->M, c->N, c->nb, c->ext_ptr, c->ext_p, S.ext_x,
+                                                                  S.leb, S.Y, x, cext);
     DDLPB_LAUNCHED(c, "ext_weights");
     return DDLPB_OK;
 }
 
 // y (+)= [K y ; K y] (forward) or y (+)= [D1 K^T (x_r + x_e) ; D2 K^T (x_r + x_e)] (transpose)
-ddlpb_status op_apply_C(ddlpb_ctx* c, const double* x, double* y, bool transpose, bool accumulate) {
+template <typename T>
+static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, bool accumulate) {
+    DDLPB_TRY(opset_prepare<T>(c, S));
     const size_t half = (size_t)c->M * c->nb;
     if (!transpose) {
-        DDLPB_TRY(op_source_multipoles(c, x, c->mu));
-        DDLPB_TRY(op_yukawa_potential(c, c->mu, c->extA));
-        DDLPB_TRY(op_masked_analysis(c, c->extA, 1.0, nullptr, y, c->nb, accumulate ? 1 : 0));
-        DDLPB_TRY(op_masked_analysis(c, c->extA, 1.0, nullptr, y + half, c->nb, accumulate ? 1 : 0));
+        DDLPB_TRY(source_mu_T<T>(c, S, x, S.mu));
+        DDLPB_TRY(yukawa_pot_T<T>(c, S, S.mu, S.extA));
+        DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y, c->nb, accumulate ? 1 : 0));
+        DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y + half, c->nb, accumulate ? 1 : 0));
         return DDLPB_OK;
     }
-    if (!accumulate) DDLPB_CK(c, cudaMemsetAsync(y, 0, sizeof(double) * 2 * half, c->stream));
+    if (!accumulate) DDLPB_CK(c, cudaMemsetAsync(y, 0, sizeof(T) * 2 * half, c->stream));
     if (c->n_src == 0) return DDLPB_OK;
-    DDLPB_TRY(op_ext_weights(c, x, c->extA));
-    DDLPB_TRY(op_yukawa_adjoint(c, c->extA, c->mu));
-    size_t smem = sizeof(double) * (c->nb + c->N) + sizeof(int) * c->N;
-    k_ct_finish<<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, c->eps1 / c->eps2, c->src, c->sph,
-                                                    c->di, c->cik, c->ext_ptr, c->ext_p, c->ext_x, c->leb, c->Y, c->mu,
-                                                    y);
+    DDLPB_TRY(ext_weights_T<T>(c, S, x, S.extA));
+    DDLPB_TRY(yukawa_adj_T<T>(c, S, S.extA, S.mu));
+    size_t smem = sizeof(T) * (c->nb + c->N) + sizeof(int) * c->N;
+    k_ct_finish<T><<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, (T)(c->eps1 / c->eps2), c->src,
+                                                       S.sph, S.di, S.cik, c->ext_ptr, c->ext_p, S.ext_x, S.leb, S.Y,
+                                                       S.mu, y);
     DDLPB_LAUNCHED(c, "ct_finish");
     return DDLPB_OK;
 }
 
-ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose) {
-    DDLPB_TRY(op_apply_AB(c, x, y, transpose, nullptr, nullptr));
-    DDLPB_TRY(op_apply_C(c, x, y, transpose, true));
+template <typename T>
+ddlpb_status op_apply_L_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose) {
+    DDLPB_TRY(op_apply_AB_T<T>(c, S, x, y, transpose, nullptr, nullptr));
+    DDLPB_TRY(apply_C_T<T>(c, S, x, y, transpose, true));
     return DDLPB_OK;
+}
+
+template ddlpb_status op_apply_L_T<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*, bool);
+template ddlpb_status op_apply_L_T<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*, bool);
+template ddlpb_status op_apply_AB_T<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*, bool, double*,
+                                            double*);
+template ddlpb_status op_apply_AB_T<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*, bool, float*, float*);
+
+// ---------------------------------------------------------------- FP64 entry points used by setup and forces
+
+ddlpb_status op_synthesis(ddlpb_ctx* c, const double* coef, int rows, double* grid, bool weighted) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return synthesis_T<double>(c, c->d64, coef, rows, grid, weighted);
+}
+
+ddlpb_status op_masked_analysis(ddlpb_ctx* c, const double* val_ext, double scale, const double* cik_scale,
+                                double* out, int out_stride, int accumulate) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return masked_analysis_T<double>(c, c->d64, val_ext, scale, cik_scale, out, out_stride, accumulate);
+}
+
+ddlpb_status op_apply_AB(ddlpb_ctx* c, const double* x, double* y, bool transpose, double* gridR, double* gridE) {
+    return op_apply_AB_T<double>(c, c->d64, x, y, transpose, gridR, gridE);
+}
+
+ddlpb_status op_source_multipoles(ddlpb_ctx* c, const double* x, double* mu) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return source_mu_T<double>(c, c->d64, x, mu);
+}
+
+ddlpb_status op_yukawa_potential(ddlpb_ctx* c, const double* mu, double* phi_ext) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return yukawa_pot_T<double>(c, c->d64, mu, phi_ext);
+}
+
+ddlpb_status op_yukawa_adjoint(ddlpb_ctx* c, const double* c_ext, double* nu) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return yukawa_adj_T<double>(c, c->d64, c_ext, nu);
+}
+
+ddlpb_status op_ext_weights(ddlpb_ctx* c, const double* x, double* cext) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return ext_weights_T<double>(c, c->d64, x, cext);
+}
+
+ddlpb_status op_apply_C(ddlpb_ctx* c, const double* x, double* y, bool transpose, bool accumulate) {
+    return apply_C_T<double>(c, c->d64, x, y, transpose, accumulate);
+}
+
+ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose) {
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    return op_apply_L_T<double>(c, c->d64, x, y, transpose);
 }

@@ -311,6 +311,11 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
             return DDLPB_EINVAL;
         }
     }
+    for (int a = 0; a < 3; ++a) {
+        double sum = 0;
+        for (int k = 0; k < M; ++k) sum += hc[3 * k + a];
+        c->centroid[a] = sum / M;
+    }
     std::vector<double4> hs(M);
     for (int k = 0; k < M; ++k)
         hs[k] = make_double4(hc[3 * k], hc[3 * k + 1], hc[3 * k + 2], hr[k] + (surface == DDLPB_SAS ? kSasProbeBohr : 0.0));

@@ -1,9 +1,11 @@
-// solve.cu -- restarted GMRES for L X = g and L* X_adj = Q, the energy, and the C ABI.
+// solve.cu -- Krylov solves of L X = g and L* X_adj = Q, the energy, and the C ABI.
 //
-// The paper solves its system with DIIS preconditioned by L_AB (Sec. 4); any Krylov
-// method that reaches the same discrete solution X gives the same energy and forces,
-// and GMRES on the full operator needs no inner solves.  The stopping rule is the
-// relative FP64 residual ||b - L x|| / ||b|| <= tol.
+// The paper solves its system with DIIS preconditioned by L_AB = diag(A, B), whose
+// inverse is applied by inner (micro) iterations (Sec. 4).  Here the outer method is
+// flexible GMRES, right-preconditioned by the same L_AB, whose inverse is applied by
+// an inner GMRES on the sparse blocks; any method that reaches the same discrete
+// solution X gives the same energy and forces.  The stopping rule is the relative
+// FP64 residual ||b - L x|| / ||b|| <= tol.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -12,16 +14,19 @@
 
 #define RBLK 256
 #define RGRID 592   // 4 x 148 resident CTAs
+#define VG 1184
+#define VB 256
 
-// partial[k * G + g] = sum over the g-th grid stride of V_k . w
-__global__ void k_multidot(long long n, int kk, const double* __restrict__ V, const double* __restrict__ w,
+// partial[k * G + g] = sum over the g-th grid stride of V_k . w (accumulated in FP64)
+template <typename T>
+__global__ void k_multidot(long long n, int kk, const T* __restrict__ V, const T* __restrict__ w,
                            double* __restrict__ partial) {
     __shared__ double red[RBLK / 32];
     const int k = blockIdx.y;
-    const double* v = V + (size_t)k * n;
+    const T* v = V + (size_t)k * n;
     double s = 0;
     for (long long i = (long long)blockIdx.x * RBLK + threadIdx.x; i < n; i += (long long)gridDim.x * RBLK)
-        s += v[i] * w[i];
+        s += (double)v[i] * (double)w[i];
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -50,44 +55,62 @@ __global__ void k_reduce(int G, const double* __restrict__ partial, double* __re
 }
 
 // w -= sum_k V_k h[k]
-__global__ void k_sub_combination(long long n, int kk, const double* __restrict__ V, const double* __restrict__ h,
-                                  double* __restrict__ w) {
-    __shared__ double sh[128];
-    for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = h[k];
+template <typename T>
+__global__ void k_sub_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ h,
+                                  T* __restrict__ w) {
+    __shared__ T sh[128];
+    for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)h[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = w[i];
+        T s = w[i];
         for (int k = 0; k < kk; ++k) s -= V[(size_t)k * n + i] * sh[k];
         w[i] = s;
     }
 }
 
 // x += sum_k V_k y[k]
-__global__ void k_add_combination(long long n, int kk, const double* __restrict__ V, const double* __restrict__ y,
-                                  double* __restrict__ x) {
-    __shared__ double sh[128];
-    for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = y[k];
+template <typename T>
+__global__ void k_add_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ y,
+                                  T* __restrict__ x) {
+    __shared__ T sh[128];
+    for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)y[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double s = x[i];
+        T s = x[i];
         for (int k = 0; k < kk; ++k) s += V[(size_t)k * n + i] * sh[k];
         x[i] = s;
     }
 }
 
 // out = a * x (+ b * y)
-__global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
-                        double* __restrict__ out) {
+template <typename T>
+__global__ void k_axpby(long long n, double a, const T* __restrict__ x, double b, const T* __restrict__ y,
+                        T* __restrict__ out) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+        out[i] = (T)(a * (double)x[i] + (y ? b * (double)y[i] : 0.0));
 }
 
 // out = x / s[0]
-__global__ void k_scale_by(long long n, const double* __restrict__ x, const double* __restrict__ s,
-                           double* __restrict__ out) {
-    double inv = 1.0 / s[0];
+template <typename T>
+__global__ void k_scale_by(long long n, const T* __restrict__ x, const double* __restrict__ s, T* __restrict__ out) {
+    T inv = (T)(1.0 / s[0]);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = x[i] * inv;
+}
+
+// FP64 <-> FP32 transfers of the refinement: r32 = r64 / s[0];  x64 += s[0] * d32
+__global__ void k_to_f32_scaled(long long n, const double* __restrict__ a, const double* __restrict__ s,
+                                float* __restrict__ b) {
+    double inv = 1.0 / s[0];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)(a[i] * inv);
+}
+
+__global__ void k_add_f32_scaled(long long n, const float* __restrict__ d, const double* __restrict__ s,
+                                 double* __restrict__ x) {
+    double sc = s[0];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += sc * (double)d[i];
 }
 
 __global__ void k_add_vec(int kk, const double* __restrict__ a, double* __restrict__ b) {
@@ -111,108 +134,141 @@ __global__ void k_energy(int M, int nb, const double* __restrict__ q, const doub
     }
 }
 
-// ---------------------------------------------------------------- host side
+// ---------------------------------------------------------------- Krylov engine
 
-static ddlpb_status dots(ddlpb_ctx* c, int kk, const double* V, const double* w, double* out, bool add, bool sq) {
+template <typename T>
+struct Krylov {
+    int m = 0;
+    long long n = 0;
+    T* V = nullptr;     // [(m+1)][n]
+    T* Z = nullptr;     // [m][n] preconditioned directions (flexible variant), or nullptr
+    T* w = nullptr;
+    T* r = nullptr;
+    double* red = nullptr;
+    double* h = nullptr;   // h1 | h2 | nrm | scalar slots
+    double* hp = nullptr;  // pinned host mirror
+};
+
+template <typename T>
+static ddlpb_status krylov_alloc(ddlpb_ctx* c, Krylov<T>& K, int m, long long n, bool flexible) {
+    K.m = m;
+    K.n = n;
+    DDLPB_TRY(ctx_alloc(c, &K.V, (size_t)(m + 1) * n));
+    if (flexible) DDLPB_TRY(ctx_alloc(c, &K.Z, (size_t)m * n));
+    DDLPB_TRY(ctx_alloc(c, &K.w, n));
+    DDLPB_TRY(ctx_alloc(c, &K.r, n));
+    DDLPB_TRY(ctx_alloc(c, &K.red, (size_t)RGRID * (m + 2)));
+    DDLPB_TRY(ctx_alloc(c, &K.h, 4 * (size_t)(m + 2)));
+    DDLPB_CK(c, cudaMallocHost((void**)&K.hp, sizeof(double) * 4 * (m + 2)));
+    c->pinned.push_back(K.hp);
+    return DDLPB_OK;
+}
+
+template <typename T>
+static ddlpb_status dots(ddlpb_ctx* c, Krylov<T>& K, int kk, const T* V, const T* w, double* out, bool sq) {
     dim3 grid(RGRID, kk);
-    k_multidot<<<grid, RBLK, 0, c->stream>>>(c->nvec, kk, V, w, c->gm_red);
+    k_multidot<T><<<grid, RBLK, 0, c->stream>>>(K.n, kk, V, w, K.red);
     DDLPB_LAUNCHED(c, "multidot");
-    k_reduce<<<kk, RBLK, 0, c->stream>>>(RGRID, c->gm_red, out, add ? 1 : 0, sq ? 1 : 0);
+    k_reduce<<<kk, RBLK, 0, c->stream>>>(RGRID, K.red, out, 0, sq ? 1 : 0);
     DDLPB_LAUNCHED(c, "reduce");
     return DDLPB_OK;
 }
 
-static ddlpb_status ensure_krylov(ddlpb_ctx* c) {
-    if (c->gm_V) return DDLPB_OK;
-    const int m = c->opt.gmres_restart;
-    DDLPB_TRY(ctx_alloc(c, &c->gm_V, (size_t)(m + 1) * c->nvec));
-    DDLPB_TRY(ctx_alloc(c, &c->gm_w, c->nvec));
-    DDLPB_TRY(ctx_alloc(c, &c->gm_r, c->nvec));
-    DDLPB_TRY(ctx_alloc(c, &c->gm_red, (size_t)RGRID * (m + 2)));
-    DDLPB_TRY(ctx_alloc(c, &c->gm_h, 4 * (size_t)(m + 2)));
-    DDLPB_CK(c, cudaMallocHost((void**)&c->h_pinned, sizeof(double) * 4 * (m + 2)));
+template <typename T>
+static ddlpb_status norm_host(ddlpb_ctx* c, Krylov<T>& K, const T* v, double* dev_slot, double* host) {
+    DDLPB_TRY(dots<T>(c, K, 1, v, v, dev_slot, true));
+    DDLPB_CK(c, cudaMemcpyAsync(K.hp + 3 * (K.m + 2), dev_slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    *host = K.hp[3 * (K.m + 2)];
     return DDLPB_OK;
 }
 
-// GMRES(m) with classical Gram-Schmidt and one re-orthogonalisation pass.
-ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double* x, int* iters, double* resid) {
-    DDLPB_TRY(ensure_krylov(c));
-    const long long n = c->nvec;
-    const int m = c->opt.gmres_restart;
+// Restarted (flexible) GMRES with classical Gram-Schmidt and one re-orthogonalisation
+// pass.  apply(in, out) is the operator, precond(in, out) the right preconditioner
+// (used only when K.Z is set).  x holds the initial guess (all zero if x_zero).
+// Stops when the Krylov estimate of ||b - A x|| / ||b|| <= tol; the true residual
+// is recomputed at every restart.
+template <typename T, typename Apply, typename Prec>
+static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precond, const T* b, T* x, double tol,
+                            int maxit, bool x_zero, int* iters, double* rel_out) {
+    const long long n = K.n;
+    const int m = K.m;
     cudaStream_t st = c->stream;
-    double* V = c->gm_V;
-    double* w = c->gm_w;
-    double* h1 = c->gm_h;            // [m+2]
-    double* h2 = c->gm_h + (m + 2);  // [m+2]
-    double* nrm = c->gm_h + 2 * (m + 2);
-    double* hp = c->h_pinned;
-    const int VG = 1184, VB = 256;
-
-    // ||b||
-    DDLPB_TRY(dots(c, 1, b, b, nrm, false, true));
-    DDLPB_CK(c, cudaMemcpyAsync(hp, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-    DDLPB_CK(c, cudaStreamSynchronize(st));
-    const double bnorm = hp[0];
+    double* h1 = K.h;
+    double* h2 = K.h + (m + 2);
+    double* nrm = K.h + 2 * (m + 2);
+    double* hp = K.hp;
+    double bnorm = 0;
+    DDLPB_TRY(norm_host<T>(c, K, b, nrm, &bnorm));
     *iters = 0;
     if (!(bnorm > 0.0)) {
-        DDLPB_CK(c, cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-        *resid = 0.0;
-        DDLPB_CK(c, cudaStreamSynchronize(st));
-        return bnorm == 0.0 ? DDLPB_OK : DDLPB_EINVAL;
+        DDLPB_CK(c, cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+        *rel_out = 0.0;
+        if (!(bnorm == 0.0)) {
+            c->err = "non-finite right-hand side";
+            return DDLPB_ENOTCONV;
+        }
+        return DDLPB_OK;
     }
-    const double tol = c->opt.tol;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), yv(m);
     int total = 0;
     double rel = 1.0;
+    bool first = true;
     for (;;) {
-        // r = b - L x ; beta = ||r||
-        DDLPB_TRY(op_apply_L(c, x, c->gm_r, transpose));
-        k_axpby<<<VG, VB, 0, st>>>(n, 1.0, b, -1.0, c->gm_r, c->gm_r);
-        DDLPB_LAUNCHED(c, "axpby");
-        DDLPB_TRY(dots(c, 1, c->gm_r, c->gm_r, nrm, false, true));
-        DDLPB_CK(c, cudaMemcpyAsync(hp, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-        DDLPB_CK(c, cudaStreamSynchronize(st));
-        const double beta = hp[0];
+        if (first && x_zero) {
+            DDLPB_CK(c, cudaMemcpyAsync(K.r, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            DDLPB_TRY(apply(x, K.r));
+            k_axpby<T><<<VG, VB, 0, st>>>(n, 1.0, b, -1.0, K.r, K.r);
+            DDLPB_LAUNCHED(c, "axpby");
+        }
+        first = false;
+        double beta = 0;
+        DDLPB_TRY(norm_host<T>(c, K, K.r, nrm, &beta));
         rel = beta / bnorm;
         if (!std::isfinite(beta)) {
             c->err = "non-finite residual in GMRES";
-            *resid = rel;
+            *rel_out = rel;
             return DDLPB_ENOTCONV;
         }
         if (rel <= tol) break;
-        if (total >= c->opt.max_iter) {
+        if (total >= maxit) {
             *iters = total;
-            *resid = rel;
-            c->err = "GMRES reached max_iter";
+            *rel_out = rel;
+            c->err = "GMRES reached max_iter (relative residual " + std::to_string(rel) + ")";
             return DDLPB_ENOTCONV;
         }
-        k_scale_by<<<VG, VB, 0, st>>>(n, c->gm_r, nrm, V);
+        k_scale_by<T><<<VG, VB, 0, st>>>(n, K.r, nrm, K.V);
         DDLPB_LAUNCHED(c, "scale");
         std::fill(gvec.begin(), gvec.end(), 0.0);
         gvec[0] = beta;
         int k = 0;
-        for (; k < m && total < c->opt.max_iter; ++k) {
+        for (; k < m && total < maxit; ++k) {
             ++total;
-            double* vk = V + (size_t)k * n;
-            DDLPB_TRY(op_apply_L(c, vk, w, transpose));
-            // CGS2
-            DDLPB_TRY(dots(c, k + 1, V, w, h1, false, false));
-            k_sub_combination<<<VG, VB, 0, st>>>(n, k + 1, V, h1, w);
+            T* vk = K.V + (size_t)k * n;
+            if (K.Z) {
+                T* zk = K.Z + (size_t)k * n;
+                DDLPB_TRY(precond(vk, zk));
+                DDLPB_TRY(apply(zk, K.w));
+            } else {
+                DDLPB_TRY(apply(vk, K.w));
+            }
+            DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h1, false));
+            k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h1, K.w);
             DDLPB_LAUNCHED(c, "sub_comb");
-            DDLPB_TRY(dots(c, k + 1, V, w, h2, false, false));
-            k_sub_combination<<<VG, VB, 0, st>>>(n, k + 1, V, h2, w);
+            DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h2, false));
+            k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h2, K.w);
             DDLPB_LAUNCHED(c, "sub_comb2");
             k_add_vec<<<1, 128, 0, st>>>(k + 1, h2, h1);
             DDLPB_LAUNCHED(c, "add_vec");
-            DDLPB_TRY(dots(c, 1, w, w, nrm, false, true));
-            k_scale_by<<<VG, VB, 0, st>>>(n, w, nrm, V + (size_t)(k + 1) * n);
+            DDLPB_TRY(dots<T>(c, K, 1, K.w, K.w, nrm, true));
+            k_scale_by<T><<<VG, VB, 0, st>>>(n, K.w, nrm, K.V + (size_t)(k + 1) * n);
             DDLPB_LAUNCHED(c, "scale2");
             DDLPB_CK(c, cudaMemcpyAsync(hp, h1, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
             DDLPB_CK(c, cudaMemcpyAsync(hp + (m + 2), nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
             DDLPB_CK(c, cudaStreamSynchronize(st));
             for (int q = 0; q <= k; ++q) H[(size_t)q * m + k] = hp[q];
             double hk1 = hp[m + 2];
-            // apply previous rotations
             for (int q = 0; q < k; ++q) {
                 double a = H[(size_t)q * m + k], bb = H[(size_t)(q + 1) * m + k];
                 H[(size_t)q * m + k] = cs[q] * a + sn[q] * bb;
@@ -235,20 +291,170 @@ ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double*
                 break;
             }
         }
-        // back substitution, x += V y
         for (int q = k - 1; q >= 0; --q) {
             double s = gvec[q];
             for (int r = q + 1; r < k; ++r) s -= H[(size_t)q * m + r] * yv[r];
             yv[q] = s / H[(size_t)q * m + q];
         }
         DDLPB_CK(c, cudaMemcpyAsync(h2, yv.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-        k_add_combination<<<VG, VB, 0, st>>>(n, k, V, h2, x);
+        k_add_combination<T><<<VG, VB, 0, st>>>(n, k, K.Z ? K.Z : K.V, h2, x);
         DDLPB_LAUNCHED(c, "add_comb");
         DDLPB_CK(c, cudaStreamSynchronize(st));
     }
     *iters = total;
-    *resid = rel;
+    *rel_out = rel;
     return DDLPB_OK;
+}
+
+struct SolverState {
+    Krylov<double> outer64, inner64;
+    Krylov<float> outer32, inner32;
+    bool ready64 = false, ready32 = false;
+    float* r32 = nullptr;
+    float* d32 = nullptr;
+    double* r64 = nullptr;
+    int inner_iters = 0;
+};
+
+static SolverState* state(ddlpb_ctx* c) {
+    if (!c->solver) c->solver = new SolverState();
+    return (SolverState*)c->solver;
+}
+
+void solver_state_free(ddlpb_ctx* c) {
+    delete (SolverState*)c->solver;
+    c->solver = nullptr;
+}
+
+static const int kInnerRestart = 40;
+static const int kInnerMaxit = 200;
+
+// Right preconditioner of Sec. 4: z = L_AB^{-1} v, L_AB = diag(A, B) (or its transpose),
+// applied by an inner GMRES on the sparse block operator (no dense coupling).
+template <typename T>
+static ddlpb_status precond_apply(ddlpb_ctx* c, OpSet<T>& S, Krylov<T>& inner, bool transpose, const T* v, T* z,
+                                  int* inner_count) {
+    int it = 0;
+    double rel = 0;
+    auto ab = [&](const T* in, T* out) { return op_apply_AB_T<T>(c, S, in, out, transpose, nullptr, nullptr); };
+    auto none = [&](const T*, T*) { return DDLPB_OK; };
+    DDLPB_CK(c, cudaMemsetAsync(z, 0, sizeof(T) * inner.n, c->stream));
+    ddlpb_status s = gmres_T<T>(c, inner, ab, none, v, z, c->opt.precond_tol, kInnerMaxit, true, &it, &rel);
+    *inner_count += it;
+    if (s == DDLPB_ENOTCONV) {
+        c->err.clear();  // an inexact preconditioner is allowed in flexible GMRES
+        return DDLPB_OK;
+    }
+    return s;
+}
+
+// FP64 flexible GMRES on L (or L*) with the L_AB preconditioner.
+static ddlpb_status solve_fp64(ddlpb_ctx* c, bool transpose, const double* b, double* x, bool x_zero, int* iters,
+                               double* resid) {
+    SolverState* S = state(c);
+    if (!S->ready64) {
+        DDLPB_TRY(krylov_alloc<double>(c, S->outer64, c->opt.gmres_restart, c->nvec, true));
+        DDLPB_TRY(krylov_alloc<double>(c, S->inner64, kInnerRestart, c->nvec, false));
+        S->ready64 = true;
+    }
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    auto L = [&](const double* in, double* out) { return op_apply_L_T<double>(c, c->d64, in, out, transpose); };
+    auto P = [&](const double* in, double* out) {
+        return precond_apply<double>(c, c->d64, S->inner64, transpose, in, out, &S->inner_iters);
+    };
+    return gmres_T<double>(c, S->outer64, L, P, b, x, c->opt.tol, c->opt.max_iter, x_zero, iters, resid);
+}
+
+// Mixed precision: FP64 iterative refinement around an FP32 flexible GMRES (FP32
+// operators, FP32 L_AB preconditioner).  Only the residual r = b - L x, the update
+// of x and the norms are FP64.
+static ddlpb_status solve_mixed(ddlpb_ctx* c, bool transpose, const double* b, double* x, bool x_zero, int* iters,
+                                double* resid, int* steps) {
+    SolverState* S = state(c);
+    const long long n = c->nvec;
+    if (!S->ready32) {
+        DDLPB_TRY(krylov_alloc<float>(c, S->outer32, c->opt.gmres_restart, n, true));
+        DDLPB_TRY(krylov_alloc<float>(c, S->inner32, kInnerRestart, n, false));
+        DDLPB_TRY(ctx_alloc(c, &S->r32, n));
+        DDLPB_TRY(ctx_alloc(c, &S->d32, n));
+        DDLPB_TRY(ctx_alloc(c, &S->r64, n));
+        if (!S->ready64) {
+            DDLPB_TRY(krylov_alloc<double>(c, S->outer64, 1, n, false));
+        }
+        S->ready32 = true;
+    }
+    DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    DDLPB_TRY(opset_prepare<float>(c, c->f32));
+    Krylov<double>& K64 = S->outer64;
+    double* slot = K64.h + 2 * (K64.m + 2);
+    double bnorm = 0;
+    DDLPB_TRY(norm_host<double>(c, K64, b, slot, &bnorm));
+    *iters = 0;
+    *steps = 0;
+    if (!(bnorm > 0.0)) {
+        DDLPB_CK(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+        *resid = 0;
+        return bnorm == 0.0 ? DDLPB_OK : DDLPB_ENOTCONV;
+    }
+    auto L32 = [&](const float* in, float* out) { return op_apply_L_T<float>(c, c->f32, in, out, transpose); };
+    auto P32 = [&](const float* in, float* out) {
+        return precond_apply<float>(c, c->f32, S->inner32, transpose, in, out, &S->inner_iters);
+    };
+    const double inner_tol = 1e-5;
+    for (int step = 0;; ++step) {
+        // r = b - L x in FP64
+        if (step == 0 && x_zero) {
+            DDLPB_CK(c, cudaMemcpyAsync(S->r64, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            DDLPB_TRY(op_apply_L_T<double>(c, c->d64, x, S->r64, transpose));
+            k_axpby<double><<<VG, VB, 0, c->stream>>>(n, 1.0, b, -1.0, S->r64, S->r64);
+            DDLPB_LAUNCHED(c, "axpby64");
+        }
+        double rn = 0;
+        DDLPB_TRY(norm_host<double>(c, K64, S->r64, slot, &rn));
+        double rel = rn / bnorm;
+        *resid = rel;
+        if (!std::isfinite(rel)) {
+            c->err = "non-finite residual in refinement";
+            return DDLPB_ENOTCONV;
+        }
+        if (rel <= c->opt.tol) break;
+        if (step >= 12 || *iters >= c->opt.max_iter) {
+            c->err = "mixed-precision refinement stalled at relative residual " + std::to_string(rel);
+            return DDLPB_ENOTCONV;
+        }
+        k_to_f32_scaled<<<VG, VB, 0, c->stream>>>(n, S->r64, slot, S->r32);
+        DDLPB_LAUNCHED(c, "to_f32");
+        DDLPB_CK(c, cudaMemsetAsync(S->d32, 0, sizeof(float) * n, c->stream));
+        int it = 0;
+        double r32rel = 0;
+        ddlpb_status st = gmres_T<float>(c, S->outer32, L32, P32, S->r32, S->d32, inner_tol,
+                                         c->opt.max_iter - *iters, true, &it, &r32rel);
+        *iters += it;
+        if (st != DDLPB_OK && st != DDLPB_ENOTCONV) return st;
+        c->err.clear();
+        k_add_f32_scaled<<<VG, VB, 0, c->stream>>>(n, S->d32, slot, x);
+        DDLPB_LAUNCHED(c, "add_f32");
+        *steps = step + 1;
+    }
+    return DDLPB_OK;
+}
+
+ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double* x, int* iters, double* resid) {
+    SolverState* S = state(c);
+    S->inner_iters = 0;
+    int steps = 0;
+    ddlpb_status s;
+    bool& zero = transpose ? c->Xa_zero : c->X_zero;
+    if (c->opt.precision == DDLPB_MIXED) {
+        s = solve_mixed(c, transpose, b, x, zero, iters, resid, &steps);
+    } else {
+        s = solve_fp64(c, transpose, b, x, zero, iters, resid);
+    }
+    zero = false;
+    c->info.refinement_steps = steps;
+    c->info.inner_iterations = S->inner_iters;
+    return s;
 }
 
 // ---------------------------------------------------------------- C ABI
@@ -264,6 +470,7 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->precision = DDLPB_FP64;
     o->fmm_order = 0;
     o->cuda_stream = nullptr;
+    o->precond_tol = 1e-3;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,
@@ -294,6 +501,7 @@ static ddlpb_status setup_common(int n, const double* centres, const double* rad
     if (o.gmres_restart < 1 || o.gmres_restart > 120) return fail("gmres_restart must be in [1, 120]");
     if (o.precision != DDLPB_FP64 && o.precision != DDLPB_MIXED) return fail("unknown precision");
     if (o.fmm_order != 0) return fail("fmm_order must be 0 (direct summation)");
+    if (!(o.precond_tol > 0.0 && o.precond_tol < 1.0)) return fail("precond_tol must be in (0, 1)");
     ddlpb_ctx* c = new ddlpb_ctx();
     c->M = n;
     c->lmax = lmax;
@@ -376,10 +584,9 @@ extern "C" ddlpb_status ddlpb_energy(ddlpb_ctx* c, double* e) {
         c->err = "ddlpb_energy before a successful ddlpb_solve";
         return DDLPB_EORDER;
     }
-    k_energy<<<1, RBLK, 0, c->stream>>>(c->M, c->nb, c->q, c->X, c->gm_h ? c->gm_h + 3 * (c->opt.gmres_restart + 2) : c->tmpv);
+    k_energy<<<1, RBLK, 0, c->stream>>>(c->M, c->nb, c->q, c->X, c->tmpv);
     DDLPB_LAUNCHED(c, "energy");
-    const double* src = c->gm_h ? c->gm_h + 3 * (c->opt.gmres_restart + 2) : c->tmpv;
-    DDLPB_CK(c, cudaMemcpyAsync(e, src, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    DDLPB_CK(c, cudaMemcpyAsync(e, c->tmpv, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     DDLPB_CK(c, cudaStreamSynchronize(c->stream));
     return DDLPB_OK;
 }
@@ -446,6 +653,7 @@ extern "C" const char* ddlpb_last_setup_error(void) { return g_setup_err.c_str()
 extern "C" void ddlpb_free(ddlpb_ctx* c) {
     if (!c) return;
     for (void* p : c->allocs) cudaFree(p);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    for (void* p : c->pinned) cudaFreeHost(p);
+    solver_state_free(c);
     delete c;
 }

@@ -110,6 +110,7 @@ def test_energy_and_forces_parity(case):
     E_ref = p.energy()
     p.adjoint()
     F_ref = p.forces()
+    case["F_ref"] = F_ref
     ctx.solve()
     E = ctx.energy()
     assert abs(E - E_ref) <= 1e-10 * abs(E_ref)
@@ -186,3 +187,29 @@ def test_error_paths():
     with pytest.raises(G.DDLPBError) as e:
         _ctx(c, rr, q, 3, 50)
     assert e.value.status == 1
+
+
+def test_mixed_precision_refinement_parity(case):
+    """FP32 Krylov solves inside FP64 refinement reach the FP64 solution: at a tight
+    tolerance the energy matches the oracle to 1e-10 relative; at the default 1e-8 the
+    mixed form stays within 1e-6 relative energy and 1e-5 relative force norm."""
+    p = case["p"]
+    if "F_ref" not in case:
+        p.solve()
+        p.adjoint()
+        case["F_ref"] = p.forces()
+    E_ref = p.energy()
+    F_ref = case["F_ref"]
+    tight = _ctx(case["c"], case["r"], case["q"], case["lmax"], case["n"], case["surf"], precision=G.DDLPB_MIXED,
+                 tol=1e-12)
+    tight.solve()
+    assert abs(tight.energy() - E_ref) <= 1e-10 * abs(E_ref)
+    info = tight.info()
+    assert info["refinement_steps"] >= 1 and info["solve_residual"] <= 1e-12
+    loose = _ctx(case["c"], case["r"], case["q"], case["lmax"], case["n"], case["surf"], precision=G.DDLPB_MIXED,
+                 tol=1e-8)
+    loose.solve()
+    assert abs(loose.energy() - E_ref) <= 1e-6 * abs(E_ref)
+    loose.adjoint()
+    F = loose.forces()
+    assert np.linalg.norm(F - F_ref) <= 1e-5 * np.linalg.norm(F_ref)
