@@ -150,6 +150,9 @@ DDLPB_API ddlpb_status ddlpb_energy_device(ddlpb_ctx* ctx, double* e);
  *   op = 3: y = [A^T x_r ; B^T x_e]
  *   op = 4: y = [C1 x_r + C2 x_e ; same]          (Eqs. definition_of_C1/C2_matrix)
  *   op = 5: y = [C1^T (x_r + x_e) ; C2^T (x_r + x_e)]
+ *   op = 8..13: the same operators in the FP32 arithmetic of the mixed-precision
+ *            form (inputs rounded to FP32, outputs widened to FP64)
+ * Errors: DDLPB_EINVAL for any other op.
  */
 DDLPB_API ddlpb_status ddlpb_apply_device(ddlpb_ctx* ctx, int op, const double* x, double* y);
 

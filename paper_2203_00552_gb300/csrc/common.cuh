@@ -400,3 +400,4 @@ ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double*
                           double* resid);
 ddlpb_status compute_forces(ddlpb_ctx* c, double* f_dev);
 void solver_state_free(ddlpb_ctx* c);
+ddlpb_status op_apply_fp32(ddlpb_ctx* c, int op, const double* x, double* y);

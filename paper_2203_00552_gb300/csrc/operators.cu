@@ -645,3 +645,27 @@ ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose
     DDLPB_TRY(opset_prepare<double>(c, c->d64));
     return op_apply_L_T<double>(c, c->d64, x, y, transpose);
 }
+
+// The FP32 operators on FP64 vectors (converted on the way in and out); used to
+// check the FP32 inner operators of the mixed-precision form against the FP64 ones.
+ddlpb_status op_apply_fp32(ddlpb_ctx* c, int op, const double* x, double* y) {
+    DDLPB_TRY(opset_prepare<float>(c, c->f32));
+    const long long n = c->nvec;
+    if (!c->f32_vec) DDLPB_TRY(ctx_alloc(c, &c->f32_vec, 2 * (size_t)n));
+    float* xf = c->f32_vec;
+    float* yf = c->f32_vec + n;
+    k_convert<double, float><<<ceil_div(n, 256), 256, 0, c->stream>>>(n, x, xf);
+    DDLPB_LAUNCHED(c, "convert_in");
+    switch (op) {
+        case 0: DDLPB_TRY(op_apply_L_T<float>(c, c->f32, xf, yf, false)); break;
+        case 1: DDLPB_TRY(op_apply_L_T<float>(c, c->f32, xf, yf, true)); break;
+        case 2: DDLPB_TRY(op_apply_AB_T<float>(c, c->f32, xf, yf, false, nullptr, nullptr)); break;
+        case 3: DDLPB_TRY(op_apply_AB_T<float>(c, c->f32, xf, yf, true, nullptr, nullptr)); break;
+        case 4: DDLPB_TRY(apply_C_T<float>(c, c->f32, xf, yf, false, false)); break;
+        case 5: DDLPB_TRY(apply_C_T<float>(c, c->f32, xf, yf, true, false)); break;
+        default: c->err = "bad operator"; return DDLPB_EINVAL;
+    }
+    k_convert<float, double><<<ceil_div(n, 256), 256, 0, c->stream>>>(n, yf, y);
+    DDLPB_LAUNCHED(c, "convert_out");
+    return DDLPB_OK;
+}

@@ -213,3 +213,17 @@ def test_mixed_precision_refinement_parity(case):
     loose.adjoint()
     F = loose.forces()
     assert np.linalg.norm(F - F_ref) <= 1e-5 * np.linalg.norm(F_ref)
+
+
+@pytest.mark.parametrize("op", range(6))
+def test_fp32_operators_track_fp64(case, op):
+    """The FP32 operators of the mixed-precision form agree with the FP64 ones to
+    single-precision accuracy (1e-5 of the output's max-norm)."""
+    ctx = case["ctx"]
+    x = _rand(ctx.nvec, 3 + op)
+    y64 = torch.empty_like(x)
+    y32 = torch.empty_like(x)
+    ctx.apply(op, x, y64)
+    ctx.apply(op + 8, x, y32)
+    scale = float(y64.abs().max())
+    assert float((y64 - y32).abs().max()) <= 1e-5 * scale
