@@ -1,0 +1,306 @@
+"""Benchmark: ddLPB energy + analytical forces, atoms/s, on the 10,000-atom globule.
+
+Workload (named in config.workload): 10,000-atom globule grown by the chain rule
+inside a 40 A ball (seed 2), vdW radii U[1.2, 2.0] A x 1.1, charges U[-0.5, 0.5] e
+with zero net charge, eps = 78.54, kappa = 0.104 1/A, lmax = 10, 590-point Lebedev
+grid, outer tolerance 1e-8 (FP64 relative residual).  One step = setup (neighbour
+lists, switch functions, hit lists, right-hand side) + primal solve + adjoint solve
++ energy + forces, from inputs already resident in HBM.  The mixed form runs the
+Krylov solves in FP32 inside FP64 iterative refinement; --precision fp64 times the
+plain FP64 path.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own copy of the workload (replicas:
+one molecule does not shard in this build); value = all atoms / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_00552_gb300 import synth  # noqa: E402
+
+METRIC = "ddLPB energy+forces atoms/s at 10k atoms (mixed vs FP64, 1e-6); served p99 ms"
+UNIT = "atoms/s"
+WORKLOAD = "globule10000"
+FP32_PEAK_TFLOPS_AT_MAX_CLOCK = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# Algorithmic FP32 flops per unit of the hot kernels (see the kernel roofline table):
+#   per (hit, basis function) for the A/B kernels (two bases, 8 flops each),
+#   per (target, source, basis function) for the Yukawa kernels.
+FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8}
+# dram bytes per launch from the committed ncu capture (profiles/), keyed by kernel, with the
+# source file digest they were taken on; null when the kernel source has changed since.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--restart", type=int, default=300)
+    ap.add_argument("--precond-tol", type=float, default=1e-1)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(w, atoms=12):
+    """The oracle (FP64, dense, CPU) on the first `atoms` atoms of the workload."""
+    from oracle import ddlpb as O
+    c, r, q = w["centres"][:atoms], w["radii"][:atoms], w["charges"][:atoms]
+    t = time.perf_counter()
+    O.run(c, r, q, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"], surface=w["surface"])
+    return time.perf_counter() - t
+
+
+def reference_arm(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    atoms = 12
+    for _ in range(args.warmup):
+        oracle_sample(w, atoms)
+    times = [oracle_sample(w, atoms) for _ in range(args.steps)]
+    dt = sum(times) / len(times)
+    value = atoms / dt
+    cores = os.cpu_count()
+    sample = ("oracle energy+forces (dense LU, FP64 numpy) on the first %d atoms of the %d-atom globule, "
+              "lmax %d, %d Lebedev points" % (atoms, w["n"], w["lmax"], w["n_lebedev"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s (oracle sample: first %d atoms)" % (args.workload, atoms), "lmax": w["lmax"],
+                       "n_lebedev": w["n_lebedev"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def clocks_start():
+    path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f, path
+    except Exception:
+        return None, None, path
+
+
+def clocks_stop(p, f, path, dev_index):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(dev_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for k, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(k)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("operators.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2203_00552_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    w = synth.workload(args.workload)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+    import torch
+    import paper_2203_00552_gb300 as G
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    if not os.path.exists(os.path.join(ROOT, "paper_2203_00552_gb300", "libddlpb.so")):
+        if rank == 0:
+            from paper_2203_00552_gb300 import build
+            build.build()
+        if pg:
+            pg.barrier()
+    G.library()
+    prec = G.DDLPB_MIXED if args.precision == "mixed" else G.DDLPB_FP64
+    opts = dict(tol=1e-8, precision=prec, gmres_restart=args.restart, precond_tol=args.precond_tol, max_iter=4000)
+    M = w["n"]
+    cen = torch.tensor(w["centres"], device=dev)
+    rad = torch.tensor(w["radii"], device=dev)
+    chg = torch.tensor(w["charges"], device=dev)
+    e_out = torch.empty(1, dtype=torch.float64, device=dev)
+    f_out = torch.empty((M, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timing=False):
+        ctx = G.Context(cen, rad, chg, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"],
+                        surface=w["surface"], stream=stream.cuda_stream, kernel_timing=1 if timing else 0, **opts)
+        ctx.solve()
+        ctx.adjoint()
+        ctx.energy_device(e_out)
+        ctx.forces_device(f_out)
+        return ctx
+
+    for _ in range(args.warmup):
+        step().close()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks_start() if rank == 0 else (None, None, None)
+    times, kstats, launches, infos = [], {}, 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctx = step(timing=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        info = ctx.info()
+        infos.append(info)
+        launches += info["kernel_launches"]
+        for base in FLOPS_PER_UNIT:
+            for suf in ("_f32", "_f64"):
+                n, ms = ctx.kernel_time(base + suf)
+                if n:
+                    a = kstats.setdefault(base + suf, [0, 0.0])
+                    a[0] += n
+                    a[1] += ms
+        ctx.close()
+    torch.cuda.synchronize()
+    clocks = clocks_stop(*clk, local) if rank == 0 else None
+    ms_step = sum(times) / len(times)
+    t_max = ms_step
+    if pg:
+        t = torch.tensor([ms_step], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t)
+    value = world * M / (t_max / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hc, hr, hq = w["centres"], w["radii"], w["charges"]
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
+    e2e_times = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = G.Context(hc, hr, hq, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"], surface=w["surface"],
+                        stream=stream.cuda_stream, **opts)
+        ctx.solve()
+        ctx.adjoint()
+        E = ctx.energy()
+        F = ctx.forces()
+        e2e_times.append(time.perf_counter() - t0)
+        ctx.close()
+    e2e = None
+    if e2e_times:
+        e2e = {"value": world * M / (sum(e2e_times) / len(e2e_times)), "unit": UNIT,
+               "h2d_bytes_per_step": int(hc.nbytes + hr.nbytes + hq.nbytes),
+               "d2h_bytes_per_step": int(F.nbytes + 8)}
+
+    # roofline of the dominant instrumented kernel
+    info = infos[-1]
+    nb = (w["lmax"] + 1) ** 2
+    units = {"ab_apply": info["n_hits"] * nb, "ab_transpose": info["n_hits"] * nb,
+             "yukawa_pot": info["n_external"] * info["n_sources"] * nb,
+             "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
+    roofline = None
+    if kstats:
+        top = max(kstats, key=lambda k: kstats[k][1])
+        n, ms = kstats[top]
+        base = top.rsplit("_", 1)[0]
+        flops_per_launch = units[base] * FLOPS_PER_UNIT[base]
+        achieved = flops_per_launch / (ms / n / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS_AT_MAX_CLOCK if top.endswith("f32") else 1.25
+        tr = NCU_TRAFFIC.get(top)
+        traffic = tr["bytes_per_launch"] if tr and tr.get("digest") == source_digest() else None
+        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "launches_per_step": n / len(times),
+                    "ms_per_launch": ms / n, "share_of_step": ms / sum(times),
+                    "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if top.endswith("f32")
+                                    else "FP64 nominal 1.25 TFLOP/s")}
+    cpu = None
+    if rank == 0 and world == 1:
+        atoms = 12
+        dt = oracle_sample(w, atoms)
+        cpu = {"value": atoms / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "oracle energy+forces (dense LU, FP64 numpy) on the first %d atoms of this workload, "
+                         "%.1f s" % (atoms, dt)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64" if prec == G.DDLPB_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "atoms": M, "lmax": w["lmax"], "n_lebedev": w["n_lebedev"],
+                           "surface": w["surface"], "precision": args.precision, "coupling": "direct summation",
+                           "tol": 1e-8, "gmres_restart": args.restart, "precond_tol": args.precond_tol,
+                           "l2": "512 MB buffer written between timed steps; working set > L2",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "cpu_baseline": cpu, "clocks": clocks,
+                "solver": {"outer": info["solve_iterations"], "adjoint_outer": info["adjoint_iterations"],
+                           "refinement": info["refinement_steps"], "residual": info["solve_residual"],
+                           "adjoint_residual": info["adjoint_residual"], "external_points": info["n_external"],
+                           "hits": info["n_hits"], "sources": info["n_sources"]},
+                "energy_hartree": float(e_out.item())}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

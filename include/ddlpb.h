@@ -62,12 +62,16 @@ typedef struct {
     double eta;          /* width of the smooth switch chi_eta (Eq. regular_char_function); default 0.1 */
     double tol;          /* relative residual ||g - L X|| / ||g|| of both solves; default 1e-8 */
     int max_iter;        /* cap on outer (FP64) Krylov iterations; default 500 */
-    int gmres_restart;   /* Krylov basis size before restart; default 40 */
+    int gmres_restart;   /* Krylov basis size before restart, 1..400; default 150 (the preconditioned
+                            spectrum is real but spread, so short restarts stagnate) */
     int precision;       /* ddlpb_precision; default DDLPB_FP64 */
     int fmm_order;       /* 0: direct summation of the dense coupling (the only mode of this build) */
     void* cuda_stream;   /* cudaStream_t the context launches on; NULL = legacy default stream */
     double precond_tol;  /* relative tolerance of the inner A/B solves that apply the L_AB
-                            preconditioner of Sec. 4 inside flexible GMRES; default 1e-3 */
+                            preconditioner of Sec. 4 inside flexible GMRES; default 1e-3;
+                            1.0 switches the preconditioner off (plain restarted GMRES) */
+    int kernel_timing;   /* nonzero: record CUDA events around every launch of the hot kernels
+                            (read with ddlpb_kernel_time); default 0 */
 } ddlpb_options;
 
 typedef struct {
@@ -83,6 +87,8 @@ typedef struct {
     double adjoint_residual;       /* final FP64 relative residual of the adjoint solve */
     int refinement_steps;          /* FP64 refinement steps of the last solve (mixed precision) */
     int inner_iterations;          /* inner A/B Krylov iterations of the last solve (preconditioner) */
+    int n_sources;                 /* spheres with at least one external point (sources of the coupling) */
+    long long kernel_launches;     /* CUDA kernels this context has launched since setup began */
 } ddlpb_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -158,6 +164,16 @@ DDLPB_API ddlpb_status ddlpb_apply_device(ddlpb_ctx* ctx, int op, const double* 
 
 /* Copy g (op 0), X (op 1) or X_adj (op 2) into device memory y (same layout as above). */
 DDLPB_API ddlpb_status ddlpb_get_vector_device(ddlpb_ctx* ctx, int which, double* y);
+
+/* Launch count and summed device time (ms, CUDA events on the context's stream) of
+ * one hot kernel since the last reset, when the context was created with
+ * kernel_timing set.  name is one of ab_apply_f32, ab_apply_f64, ab_transpose_f32,
+ * ab_transpose_f64, yukawa_pot_f32, yukawa_pot_f64, yukawa_adj_f32, yukawa_adj_f64;
+ * an unknown or unused name gives 0 launches.  Synchronises the stream. */
+DDLPB_API ddlpb_status ddlpb_kernel_time(ddlpb_ctx* ctx, const char* name, long long* launches, double* ms);
+
+/* Reset the kernel timers. */
+DDLPB_API ddlpb_status ddlpb_kernel_time_reset(ddlpb_ctx* ctx);
 
 /* Counters and solver statistics. */
 DDLPB_API ddlpb_status ddlpb_get_info(const ddlpb_ctx* ctx, ddlpb_info* info);

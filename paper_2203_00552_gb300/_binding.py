@@ -26,7 +26,7 @@ OP_L, OP_LT, OP_AB, OP_ABT, OP_C, OP_CT = range(6)
 class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int), ("gmres_restart", C.c_int),
                 ("precision", C.c_int), ("fmm_order", C.c_int), ("cuda_stream", C.c_void_p),
-                ("precond_tol", C.c_double)]
+                ("precond_tol", C.c_double), ("kernel_timing", C.c_int)]
 
 
 class Info(C.Structure):
@@ -34,7 +34,8 @@ class Info(C.Structure):
                 ("n_neighbour_pairs", C.c_longlong), ("n_hits", C.c_longlong), ("n_external", C.c_longlong),
                 ("solve_iterations", C.c_int), ("adjoint_iterations", C.c_int), ("solve_residual", C.c_double),
                 ("adjoint_residual", C.c_double), ("refinement_steps", C.c_int),
-                ("inner_iterations", C.c_int)]
+                ("inner_iterations", C.c_int), ("n_sources", C.c_int),
+                ("kernel_launches", C.c_longlong)]
 
 
 class DDLPBError(RuntimeError):
@@ -47,7 +48,8 @@ _lib = None
 
 EXPORTS = ["ddlpb_default_options", "ddlpb_setup", "ddlpb_setup_device", "ddlpb_solve", "ddlpb_adjoint",
            "ddlpb_energy", "ddlpb_energy_device", "ddlpb_forces", "ddlpb_forces_device", "ddlpb_apply_device",
-           "ddlpb_get_vector_device", "ddlpb_get_info", "ddlpb_last_error", "ddlpb_last_setup_error", "ddlpb_free"]
+           "ddlpb_get_vector_device", "ddlpb_get_info", "ddlpb_last_error", "ddlpb_last_setup_error", "ddlpb_free",
+           "ddlpb_kernel_time", "ddlpb_kernel_time_reset"]
 
 
 def library():
@@ -86,6 +88,10 @@ def library():
     lib.ddlpb_last_setup_error.restype = C.c_char_p
     lib.ddlpb_free.argtypes = [P]
     lib.ddlpb_free.restype = None
+    lib.ddlpb_kernel_time.argtypes = [P, C.c_char_p, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
+    lib.ddlpb_kernel_time.restype = C.c_int
+    lib.ddlpb_kernel_time_reset.argtypes = [P]
+    lib.ddlpb_kernel_time_reset.restype = C.c_int
     _lib = lib
     return lib
 
@@ -180,6 +186,16 @@ class Context:
         i = Info()
         self._check(library().ddlpb_get_info(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def kernel_time(self, name: str):
+        """(launches, total ms) of one hot kernel since the last reset (needs kernel_timing=1)."""
+        n = C.c_longlong()
+        ms = C.c_double()
+        self._check(library().ddlpb_kernel_time(self._h, name.encode(), C.byref(n), C.byref(ms)))
+        return int(n.value), float(ms.value)
+
+    def kernel_time_reset(self):
+        self._check(library().ddlpb_kernel_time_reset(self._h))
 
     def close(self):
         if self._h:

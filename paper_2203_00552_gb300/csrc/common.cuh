@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,14 @@ struct ForceScratch {
     double *G = nullptr, *muC = nullptr, *nu = nullptr, *muc = nullptr;
     double4* fs = nullptr;
     int* extpos = nullptr;
+};
+
+// Per-kernel launch timing (CUDA events on the context's stream), enabled by
+// ddlpb_options.kernel_timing.
+struct KernelTimes {
+    std::vector<cudaEvent_t> ev;  // start, end pairs not yet read
+    long long launches = 0;
+    double ms = 0.0;
 };
 
 struct ddlpb_ctx {
@@ -144,6 +153,7 @@ struct ddlpb_ctx {
     OpSet<double> d64;          // aliases the double tables above
     OpSet<float> f32;           // built on first use by the mixed-precision solve
     double centroid[3] = {0, 0, 0};
+    std::map<std::string, KernelTimes> ktimes;
     float* f32_vec = nullptr;   // FP32 Krylov workspace
 };
 
@@ -160,6 +170,7 @@ struct ddlpb_ctx {
 
 #define DDLPB_LAUNCHED(ctx, name)                                                  \
     do {                                                                           \
+        ++(ctx)->info.kernel_launches;                                             \
         cudaError_t e__ = cudaGetLastError();                                      \
         if (e__ != cudaSuccess) {                                                  \
             (ctx)->err = std::string("launch ") + name + ": " + cudaGetErrorString(e__); \
@@ -189,6 +200,27 @@ static ddlpb_status ctx_alloc(ddlpb_ctx* c, T** p, size_t count) {
 }
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Event pair around one launch when kernel timing is on.
+struct KernelTimer {
+    ddlpb_ctx* c;
+    cudaEvent_t e1 = nullptr;
+    KernelTimer(ddlpb_ctx* ctx, const char* name, bool fp32) : c(ctx) {
+        if (!c->opt.kernel_timing) return;
+        cudaEvent_t e0;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            e1 = nullptr;
+            return;
+        }
+        KernelTimes& k = c->ktimes[std::string(name) + (fp32 ? "_f32" : "_f64")];
+        k.ev.push_back(e0);
+        k.ev.push_back(e1);
+        cudaEventRecord(e0, c->stream);
+    }
+    ~KernelTimer() {
+        if (e1) cudaEventRecord(e1, c->stream);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Device math.

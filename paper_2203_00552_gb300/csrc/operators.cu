@@ -501,6 +501,7 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     if (!transpose) {
         size_t smem = sizeof(T) * (2 * (size_t)c->N + 2 * (size_t)(L + 1) * BLK);
         DDLPB_TRY(set_smem(c, (const void*)k_ab_apply<T, typename OpSet<T>::V4>, smem));
+        KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
         k_ab_apply<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
                                                       c->hit_ptr, c->hit_j, S.hit_w, S.Sinv, S.Y, x, y, gridR, gridE);
         DDLPB_LAUNCHED(c, "ab_apply");
@@ -510,6 +511,7 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
     size_t smem = sizeof(T) * (2 * (size_t)(BLK / 32) * c->nb + 2 * (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_ab_transpose<T, typename OpSet<T>::V4>, smem));
+    KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
     k_ab_transpose<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
                                                       c->thit_ptr, c->thit_p, S.thit_w, S.Sinv, S.gridA, S.gridB, x,
                                                       y);
@@ -536,6 +538,7 @@ static ddlpb_status yukawa_pot_T(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_
     size_t smem = sizeof(V4) * YK_TS + sizeof(T) * (YK_TS * (size_t)c->nb + YK_TS * (size_t)(L + 2) +
                                                      (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_yukawa_pot<T, V4>, smem));
+    KernelTimer kt(c, "yukawa_pot", sizeof(T) == 4);
     k_yukawa_pot<T><<<ceil_div(c->E, BLK), BLK, smem, c->stream>>>(c->E, S.ext_x, c->n_src, c->src, S.sph, mu,
                                                                    S.Khinv, c->nb, L, (T)c->kappa, S.yt, phi_ext);
     DDLPB_LAUNCHED(c, "yukawa_pot");
@@ -549,6 +552,7 @@ static ddlpb_status yukawa_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* n
     using V4 = typename OpSet<T>::V4;
     size_t smem = sizeof(T) * ((size_t)(BLK / 32) * c->nb + (L + 2) + (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_yukawa_adj<T, V4>, smem));
+    KernelTimer kt(c, "yukawa_adj", sizeof(T) == 4);
     k_yukawa_adj<T><<<c->n_src, BLK, smem, c->stream>>>(c->E, S.ext_x, c_ext, c->src, S.sph, S.Khinv, c->nb, L,
                                                         (T)c->kappa, S.yt, nu);
     DDLPB_LAUNCHED(c, "yukawa_adj");

@@ -495,5 +495,6 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
     c->info.n_neighbour_pairs = c->n_pairs;
     c->info.n_hits = c->H;
     c->info.n_external = c->E;
+    c->info.n_sources = c->n_src;
     return DDLPB_OK;
 }

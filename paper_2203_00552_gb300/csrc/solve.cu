@@ -11,7 +11,20 @@
 #include <cstring>
 #include <vector>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "common.cuh"
+
+// DDLPB_TRACE=1 in the environment prints the restart residuals of every Krylov solve.
+static bool trace_on() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("DDLPB_TRACE");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
+}
 
 #define RBLK 256
 #define RGRID 592   // 4 x 148 resident CTAs
@@ -59,7 +72,7 @@ __global__ void k_reduce(int G, const double* __restrict__ partial, double* __re
 template <typename T>
 __global__ void k_sub_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ h,
                                   T* __restrict__ w) {
-    __shared__ T sh[128];
+    __shared__ T sh[512];
     for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)h[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -73,7 +86,7 @@ __global__ void k_sub_combination(long long n, int kk, const T* __restrict__ V, 
 template <typename T>
 __global__ void k_add_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ y,
                                   T* __restrict__ x) {
-    __shared__ T sh[128];
+    __shared__ T sh[512];
     for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)y[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -115,7 +128,7 @@ __global__ void k_add_f32_scaled(long long n, const float* __restrict__ d, const
 }
 
 __global__ void k_add_vec(int kk, const double* __restrict__ a, double* __restrict__ b) {
-    int k = threadIdx.x;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < kk) b[k] += a[k];
 }
 
@@ -191,7 +204,7 @@ static ddlpb_status norm_host(ddlpb_ctx* c, Krylov<T>& K, const T* v, double* de
 // is recomputed at every restart.
 template <typename T, typename Apply, typename Prec>
 static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precond, const T* b, T* x, double tol,
-                            int maxit, bool x_zero, int* iters, double* rel_out) {
+                            int maxit, bool x_zero, int* iters, double* rel_out, bool stall_exit = false) {
     const long long n = K.n;
     const int m = K.m;
     cudaStream_t st = c->stream;
@@ -213,7 +226,7 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
     }
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), yv(m);
     int total = 0;
-    double rel = 1.0;
+    double rel = 1.0, prev_rel = -1.0;
     bool first = true;
     for (;;) {
         if (first && x_zero) {
@@ -227,12 +240,22 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
         double beta = 0;
         DDLPB_TRY(norm_host<T>(c, K, K.r, nrm, &beta));
         rel = beta / bnorm;
+        if (trace_on())
+            std::fprintf(stderr, "[ddlpb] gmres<%s>%s m=%d it=%d true_rel=%.3e tol=%.1e\n",
+                         sizeof(T) == 8 ? "f64" : "f32", K.Z ? " flexible" : "", m, total, rel, tol);
         if (!std::isfinite(beta)) {
             c->err = "non-finite residual in GMRES";
             *rel_out = rel;
             return DDLPB_ENOTCONV;
         }
         if (rel <= tol) break;
+        if (stall_exit && prev_rel > 0 && rel > 0.5 * prev_rel) {
+            *iters = total;
+            *rel_out = rel;
+            c->err = "GMRES stagnated (relative residual " + std::to_string(rel) + ")";
+            return DDLPB_ENOTCONV;
+        }
+        prev_rel = rel;
         if (total >= maxit) {
             *iters = total;
             *rel_out = rel;
@@ -260,7 +283,7 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
             DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h2, false));
             k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h2, K.w);
             DDLPB_LAUNCHED(c, "sub_comb2");
-            k_add_vec<<<1, 128, 0, st>>>(k + 1, h2, h1);
+            k_add_vec<<<ceil_div(k + 1, 256), 256, 0, st>>>(k + 1, h2, h1);
             DDLPB_LAUNCHED(c, "add_vec");
             DDLPB_TRY(dots<T>(c, K, 1, K.w, K.w, nrm, true));
             k_scale_by<T><<<VG, VB, 0, st>>>(n, K.w, nrm, K.V + (size_t)(k + 1) * n);
@@ -363,6 +386,11 @@ static ddlpb_status solve_fp64(ddlpb_ctx* c, bool transpose, const double* b, do
     auto P = [&](const double* in, double* out) {
         return precond_apply<double>(c, c->d64, S->inner64, transpose, in, out, &S->inner_iters);
     };
+    if (c->opt.precond_tol >= 1.0) {
+        Krylov<double> plain = S->outer64;
+        plain.Z = nullptr;
+        return gmres_T<double>(c, plain, L, P, b, x, c->opt.tol, c->opt.max_iter, x_zero, iters, resid);
+    }
     return gmres_T<double>(c, S->outer64, L, P, b, x, c->opt.tol, c->opt.max_iter, x_zero, iters, resid);
 }
 
@@ -401,10 +429,11 @@ static ddlpb_status solve_mixed(ddlpb_ctx* c, bool transpose, const double* b, d
     auto P32 = [&](const float* in, float* out) {
         return precond_apply<float>(c, c->f32, S->inner32, transpose, in, out, &S->inner_iters);
     };
-    // FP32 operators carry ~1e-6 relative error, so each refinement step asks the FP32
-    // Krylov solve for 1e-4: about four digits gained per FP64 residual evaluation.
-    const double inner_tol = 1e-4;
-    const int step_cap = std::max(50, c->opt.max_iter);
+    // The attainable accuracy of an FP32 Krylov solve is about cond(L) * 6e-8; on dense
+    // globules at lmax = 10 that is ~1e-4, so each refinement step asks for 1e-3 (three
+    // digits per FP64 residual evaluation) and stops early if a restart shows no progress.
+    const double inner_tol = 1e-3;
+    const int step_cap = c->opt.max_iter;
     for (int step = 0;; ++step) {
         // r = b - L x in FP64
         if (step == 0 && x_zero) {
@@ -418,12 +447,13 @@ static ddlpb_status solve_mixed(ddlpb_ctx* c, bool transpose, const double* b, d
         DDLPB_TRY(norm_host<double>(c, K64, S->r64, slot, &rn));
         double rel = rn / bnorm;
         *resid = rel;
+        if (trace_on()) std::fprintf(stderr, "[ddlpb] refinement step %d fp64_rel=%.3e\n", step, rel);
         if (!std::isfinite(rel)) {
             c->err = "non-finite residual in refinement";
             return DDLPB_ENOTCONV;
         }
         if (rel <= c->opt.tol) break;
-        if (step >= 12) {
+        if (step >= 20) {
             c->err = "mixed-precision refinement stalled at relative residual " + std::to_string(rel);
             return DDLPB_ENOTCONV;
         }
@@ -432,8 +462,10 @@ static ddlpb_status solve_mixed(ddlpb_ctx* c, bool transpose, const double* b, d
         DDLPB_CK(c, cudaMemsetAsync(S->d32, 0, sizeof(float) * n, c->stream));
         int it = 0;
         double r32rel = 0;
-        ddlpb_status st = gmres_T<float>(c, S->outer32, L32, P32, S->r32, S->d32, inner_tol, step_cap, true, &it,
-                                         &r32rel);
+        Krylov<float> K32 = S->outer32;
+        if (c->opt.precond_tol >= 1.0) K32.Z = nullptr;   // plain GMRES, no L_AB preconditioner
+        ddlpb_status st = gmres_T<float>(c, K32, L32, P32, S->r32, S->d32, inner_tol, step_cap, true, &it, &r32rel,
+                                         true);
         *iters += it;
         if (st != DDLPB_OK && st != DDLPB_ENOTCONV) return st;
         c->err.clear();
@@ -470,11 +502,12 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->eta = 0.1;
     o->tol = 1e-8;
     o->max_iter = 500;
-    o->gmres_restart = 40;
+    o->gmres_restart = 150;
     o->precision = DDLPB_FP64;
     o->fmm_order = 0;
     o->cuda_stream = nullptr;
     o->precond_tol = 1e-3;
+    o->kernel_timing = 0;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,
@@ -502,10 +535,10 @@ static ddlpb_status setup_common(int n, const double* centres, const double* rad
     if (!(o.eta > 0.0 && o.eta <= 1.0)) return fail("eta must be in (0, 1]");
     if (!(o.tol > 0.0)) return fail("tol must be > 0");
     if (o.max_iter < 1) return fail("max_iter must be >= 1");
-    if (o.gmres_restart < 1 || o.gmres_restart > 120) return fail("gmres_restart must be in [1, 120]");
+    if (o.gmres_restart < 1 || o.gmres_restart > 400) return fail("gmres_restart must be in [1, 400]");
     if (o.precision != DDLPB_FP64 && o.precision != DDLPB_MIXED) return fail("unknown precision");
     if (o.fmm_order != 0) return fail("fmm_order must be 0 (direct summation)");
-    if (!(o.precond_tol > 0.0 && o.precond_tol < 1.0)) return fail("precond_tol must be in (0, 1)");
+    if (!(o.precond_tol > 0.0 && o.precond_tol <= 1.0)) return fail("precond_tol must be in (0, 1]");
     ddlpb_ctx* c = new ddlpb_ctx();
     c->M = n;
     c->lmax = lmax;
@@ -649,6 +682,38 @@ extern "C" ddlpb_status ddlpb_get_vector_device(ddlpb_ctx* c, int which, double*
     return DDLPB_OK;
 }
 
+extern "C" ddlpb_status ddlpb_kernel_time(ddlpb_ctx* c, const char* name, long long* launches, double* ms) {
+    if (!c || !name || !launches || !ms) return DDLPB_EINVAL;
+    *launches = 0;
+    *ms = 0.0;
+    auto it = c->ktimes.find(name);
+    if (it == c->ktimes.end()) return DDLPB_OK;
+    KernelTimes& k = it->second;
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i + 1 < k.ev.size(); i += 2) {
+        float t = 0.f;
+        DDLPB_CK(c, cudaEventElapsedTime(&t, k.ev[i], k.ev[i + 1]));
+        k.ms += t;
+        k.launches += 1;
+        cudaEventDestroy(k.ev[i]);
+        cudaEventDestroy(k.ev[i + 1]);
+    }
+    k.ev.clear();
+    *launches = k.launches;
+    *ms = k.ms;
+    return DDLPB_OK;
+}
+
+extern "C" ddlpb_status ddlpb_kernel_time_reset(ddlpb_ctx* c) {
+    if (!c) return DDLPB_EINVAL;
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    for (auto& kv : c->ktimes) {
+        for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+        kv.second = KernelTimes();
+    }
+    return DDLPB_OK;
+}
+
 extern "C" ddlpb_status ddlpb_get_info(const ddlpb_ctx* c, ddlpb_info* info) {
     if (!c || !info) return DDLPB_EINVAL;
     *info = c->info;
@@ -661,6 +726,8 @@ extern "C" const char* ddlpb_last_setup_error(void) { return g_setup_err.c_str()
 
 extern "C" void ddlpb_free(ddlpb_ctx* c) {
     if (!c) return;
+    for (auto& kv : c->ktimes)
+        for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     for (void* p : c->pinned) cudaFreeHost(p);
     solver_state_free(c);
