@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--precond-tol", type=float, default=1e-1)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--ops-only", action="store_true",
+                    help="setup plus one application of each FP32 operator, then exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -184,6 +187,18 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 512 MB > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
+    if args.ops_only:
+        ctx = G.Context(cen, rad, chg, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"],
+                        surface=w["surface"], stream=stream.cuda_stream, **opts)
+        x = torch.randn(ctx.nvec, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        for op in (10, 11, 12, 13):
+            ctx.apply(op, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"ops_only": args.workload, "info": ctx.info()}), flush=True)
+        ctx.close()
+        return
+
     def step(timing=False):
         ctx = G.Context(cen, rad, chg, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"],
                         surface=w["surface"], stream=stream.cuda_stream, kernel_timing=1 if timing else 0, **opts)
@@ -274,7 +289,7 @@ def main():
                     "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if top.endswith("f32")
                                     else "FP64 nominal 1.25 TFLOP/s")}
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         atoms = 12
         dt = oracle_sample(w, atoms)
         cpu = {"value": atoms / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
