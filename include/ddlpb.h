@@ -72,6 +72,10 @@ typedef struct {
                             1.0 switches the preconditioner off (plain restarted GMRES) */
     int kernel_timing;   /* nonzero: record CUDA events around every launch of the hot kernels
                             (read with ddlpb_kernel_time); default 0 */
+    int precond_coupling; /* nonzero: the preconditioner also holds the coupling C1/C2 between
+                            each sphere and its neighbours (sources j in N_i and i itself);
+                            0: L_AB = diag(A, B) only, as in Sec. 4; default 0 (with an
+                            iterative inner solve the near coupling slows convergence down) */
 } ddlpb_options;
 
 typedef struct {

@@ -415,6 +415,7 @@ template <typename T> ddlpb_status opset_prepare(ddlpb_ctx* c, OpSet<T>& S);
 template <typename T> ddlpb_status op_apply_L_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose);
 template <typename T>
 ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE);
+template <typename T> ddlpb_status op_apply_P_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose);
 ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const double* radii,
                                   const double* charges, bool device_ptrs, int surface);
 ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose);

@@ -313,6 +313,87 @@ __global__ void k_yukawa_adj(int E, const V4* __restrict__ ext_x, const T* __res
     }
 }
 
+// The near part of the coupling, used inside the preconditioner: for an external point t
+// of sphere i, phi_loc(t) = sum over j in {i} and N_i of mu_j . B^k_j(x_t).  mu_j is zero
+// for spheres without external points.  One CTA per sphere i.
+template <typename T, typename V4>
+__global__ void k_yukawa_local(int N, int nb, int L, T kappa, const int* __restrict__ ext_ptr,
+                               const V4* __restrict__ ext_x, const int* __restrict__ nptr,
+                               const int* __restrict__ nidx, const V4* __restrict__ sph, const T* __restrict__ mu,
+                               const T* __restrict__ Khinv, YTabT<T> yt, T* __restrict__ phi) {
+    extern __shared__ unsigned char smraw[];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    T* rad = (T*)smraw;
+    const int i = blockIdx.x;
+    const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+    const int k0 = nptr[i], nn = nptr[i + 1] - k0;
+    for (int t = t0 + tid; t < t0 + cnt; t += bd) {
+        V4 xt = ext_x[t];
+        T acc = 0;
+        for (int k = -1; k < nn; ++k) {
+            int j = k < 0 ? i : nidx[k0 + k];
+            V4 b = sph[j];
+            T dx = xt.x - b.x, dy = xt.y - b.y, dz = xt.z - b.z;
+            T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(2, L, rho, b.w, kappa, Khinv + (size_t)j * (L + 2), rad + tid, nullptr, bd);
+            const T* m = mu + (size_t)j * nb;
+            T v = 0;
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
+                          [&](int idx, int l, T yv) { v += __ldg(m + idx) * rad[tid + l * bd] * yv; });
+            acc += v;
+        }
+        phi[t] = acc;
+    }
+}
+
+// Transpose of k_yukawa_local: nu_j = sum over i in {j} and N_j, t external on i, of
+// c_t B^k_j(x_t).  One CTA per source sphere j (the neighbour relation is symmetric).
+template <typename T, typename V4>
+__global__ void k_yukawa_local_adj(int nb, int L, T kappa, const int* __restrict__ src,
+                                   const int* __restrict__ ext_ptr, const V4* __restrict__ ext_x,
+                                   const T* __restrict__ cext, const int* __restrict__ nptr,
+                                   const int* __restrict__ nidx, const V4* __restrict__ sph,
+                                   const T* __restrict__ Khinv, YTabT<T> yt, T* __restrict__ nu) {
+    extern __shared__ unsigned char smraw[];
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+    T* acc = (T*)smraw;
+    T* kh = acc + nw * nb;
+    T* rad = kh + (L + 2);
+    const int j = src[blockIdx.x];
+    const V4 b = sph[j];
+    for (int k = tid; k < nw * nb; k += bd) acc[k] = 0;
+    for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
+    __syncthreads();
+    const int k0 = nptr[j], nn = nptr[j + 1] - k0;
+    for (int k = -1; k < nn; ++k) {
+        const int i = k < 0 ? j : nidx[k0 + k];
+        const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+        for (int base = 0; base < cnt; base += bd) {
+            int t = t0 + base + tid;
+            T dx = b.w, dy = 0, dz = 0, c = 0;
+            if (base + tid < cnt) {
+                V4 xt = ext_x[t];
+                dx = xt.x - b.x;
+                dy = xt.y - b.y;
+                dz = xt.z - b.z;
+                c = cext[t];
+            }
+            T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(2, L, rho, b.w, kappa, kh, rad + tid, nullptr, bd);
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
+                T v = warp_sum(c * rad[tid + l * bd] * yv);
+                if (lane == 0) acc[warp * nb + idx] += v;
+            });
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nb; idx += bd) {
+        T s = 0;
+        for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
+        nu[(size_t)j * nb + idx] = s;
+    }
+}
+
 // c_t = w_n chi_t sum_lm Y_lm(s_n) (x_r + x_e)_{i lm} at the external points of sphere i.
 template <typename T, typename V4>
 __global__ void k_ext_weights(int M, int N, int nb, const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
@@ -567,14 +648,42 @@ static ddlpb_status ext_weights_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* cext
     return DDLPB_OK;
 }
 
-// y (+)= [K y ; K y] (forward) or y (+)= [D1 K^T (x_r + x_e) ; D2 K^T (x_r + x_e)] (transpose)
 template <typename T>
-static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, bool accumulate) {
+static ddlpb_status yukawa_local_T(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
+    if (c->E == 0) return DDLPB_OK;
+    size_t smem = sizeof(T) * (size_t)(c->lmax + 1) * BLK;
+    KernelTimer kt(c, "yukawa_local", sizeof(T) == 4);
+    k_yukawa_local<T><<<c->M, BLK, smem, c->stream>>>(c->N, c->nb, c->lmax, (T)c->kappa, c->ext_ptr, S.ext_x,
+                                                      c->nbr_ptr, c->nbr_idx, S.sph, mu, S.Khinv, S.yt, phi_ext);
+    DDLPB_LAUNCHED(c, "yukawa_local");
+    return DDLPB_OK;
+}
+
+template <typename T>
+static ddlpb_status yukawa_local_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
+    if (c->n_src == 0) return DDLPB_OK;
+    const int L = c->lmax;
+    using V4 = typename OpSet<T>::V4;
+    size_t smem = sizeof(T) * ((size_t)(BLK / 32) * c->nb + (L + 2) + (size_t)(L + 1) * BLK);
+    DDLPB_TRY(set_smem(c, (const void*)k_yukawa_local_adj<T, V4>, smem));
+    k_yukawa_local_adj<T><<<c->n_src, BLK, smem, c->stream>>>(c->nb, L, (T)c->kappa, c->src, c->ext_ptr, S.ext_x,
+                                                              c_ext, c->nbr_ptr, c->nbr_idx, S.sph, S.Khinv, S.yt,
+                                                              nu);
+    DDLPB_LAUNCHED(c, "yukawa_local_adj");
+    return DDLPB_OK;
+}
+
+// y (+)= [K y ; K y] (forward) or y (+)= [D1 K^T (x_r + x_e) ; D2 K^T (x_r + x_e)] (transpose).
+// With local, K keeps only the sources j in {i} and N_i of each target sphere i.
+template <typename T>
+static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, bool accumulate,
+                              bool local = false) {
     DDLPB_TRY(opset_prepare<T>(c, S));
     const size_t half = (size_t)c->M * c->nb;
     if (!transpose) {
         DDLPB_TRY(source_mu_T<T>(c, S, x, S.mu));
-        DDLPB_TRY(yukawa_pot_T<T>(c, S, S.mu, S.extA));
+        if (local) DDLPB_TRY(yukawa_local_T<T>(c, S, S.mu, S.extA));
+        else DDLPB_TRY(yukawa_pot_T<T>(c, S, S.mu, S.extA));
         DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y, c->nb, accumulate ? 1 : 0));
         DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y + half, c->nb, accumulate ? 1 : 0));
         return DDLPB_OK;
@@ -582,7 +691,8 @@ static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool 
     if (!accumulate) DDLPB_CK(c, cudaMemsetAsync(y, 0, sizeof(T) * 2 * half, c->stream));
     if (c->n_src == 0) return DDLPB_OK;
     DDLPB_TRY(ext_weights_T<T>(c, S, x, S.extA));
-    DDLPB_TRY(yukawa_adj_T<T>(c, S, S.extA, S.mu));
+    if (local) DDLPB_TRY(yukawa_local_adj_T<T>(c, S, S.extA, S.mu));
+    else DDLPB_TRY(yukawa_adj_T<T>(c, S, S.extA, S.mu));
     size_t smem = sizeof(T) * (c->nb + c->N) + sizeof(int) * c->N;
     k_ct_finish<T><<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, (T)(c->eps1 / c->eps2), c->src,
                                                        S.sph, S.di, S.cik, c->ext_ptr, c->ext_p, S.ext_x, S.leb, S.Y,
@@ -598,6 +708,17 @@ ddlpb_status op_apply_L_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tran
     return DDLPB_OK;
 }
 
+// The operator of the preconditioner: [A x_r ; B x_e] plus the near part of the coupling
+// (or the transposes).
+template <typename T>
+ddlpb_status op_apply_P_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose) {
+    DDLPB_TRY(op_apply_AB_T<T>(c, S, x, y, transpose, nullptr, nullptr));
+    DDLPB_TRY(apply_C_T<T>(c, S, x, y, transpose, true, true));
+    return DDLPB_OK;
+}
+
+template ddlpb_status op_apply_P_T<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*, bool);
+template ddlpb_status op_apply_P_T<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*, bool);
 template ddlpb_status op_apply_L_T<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*, bool);
 template ddlpb_status op_apply_L_T<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*, bool);
 template ddlpb_status op_apply_AB_T<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*, bool, double*,

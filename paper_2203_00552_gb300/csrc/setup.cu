@@ -464,6 +464,7 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
     DDLPB_TRY(ctx_alloc(c, &c->S0, E));
     DDLPB_TRY(ctx_alloc(c, &c->extA, E));
     DDLPB_TRY(ctx_alloc(c, &c->extB, E));
+    DDLPB_CK(c, cudaMemsetAsync(c->mu, 0, sizeof(double) * half, st));
     DDLPB_CK(c, cudaMemsetAsync(c->X, 0, sizeof(double) * c->nvec, st));
     DDLPB_CK(c, cudaMemsetAsync(c->Xa, 0, sizeof(double) * c->nvec, st));
     DDLPB_CK(c, cudaMemsetAsync(c->Qv, 0, sizeof(double) * c->nvec, st));

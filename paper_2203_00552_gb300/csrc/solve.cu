@@ -353,14 +353,18 @@ void solver_state_free(ddlpb_ctx* c) {
 static const int kInnerRestart = 40;
 static const int kInnerMaxit = 200;
 
-// Right preconditioner of Sec. 4: z = L_AB^{-1} v, L_AB = diag(A, B) (or its transpose),
-// applied by an inner GMRES on the sparse block operator (no dense coupling).
+// Right preconditioner: z = P^{-1} v with P = L_AB = diag(A, B) of Sec. 4, plus (when
+// precond_coupling is set) the near part of the coupling C1/C2 between each sphere and
+// its neighbours; applied by an inner GMRES on that sparse operator.
 template <typename T>
 static ddlpb_status precond_apply(ddlpb_ctx* c, OpSet<T>& S, Krylov<T>& inner, bool transpose, const T* v, T* z,
                                   int* inner_count) {
     int it = 0;
     double rel = 0;
-    auto ab = [&](const T* in, T* out) { return op_apply_AB_T<T>(c, S, in, out, transpose, nullptr, nullptr); };
+    auto ab = [&](const T* in, T* out) {
+        if (c->opt.precond_coupling) return op_apply_P_T<T>(c, S, in, out, transpose);
+        return op_apply_AB_T<T>(c, S, in, out, transpose, nullptr, nullptr);
+    };
     auto none = [&](const T*, T*) { return DDLPB_OK; };
     DDLPB_CK(c, cudaMemsetAsync(z, 0, sizeof(T) * inner.n, c->stream));
     ddlpb_status s = gmres_T<T>(c, inner, ab, none, v, z, c->opt.precond_tol, kInnerMaxit, true, &it, &rel);
@@ -508,6 +512,7 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->cuda_stream = nullptr;
     o->precond_tol = 1e-3;
     o->kernel_timing = 0;
+    o->precond_coupling = 0;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,
