@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ["ddlpb_default_options", "ddlpb_setup", "ddlpb_setup_device", "ddlpb_solve", "ddlpb_adjoint",
            "ddlpb_energy", "ddlpb_energy_device", "ddlpb_forces", "ddlpb_forces_device", "ddlpb_apply_device",
            "ddlpb_get_vector_device", "ddlpb_get_info", "ddlpb_last_error", "ddlpb_last_setup_error", "ddlpb_free",
-           "ddlpb_kernel_time", "ddlpb_kernel_time_reset"]
+           "ddlpb_kernel_time", "ddlpb_kernel_time_reset", "ddlpb_energy_noalloc", "ddlpb_noalloc_last_error"]
 
 
 def library():
@@ -92,6 +92,10 @@ def library():
     lib.ddlpb_kernel_time.restype = C.c_int
     lib.ddlpb_kernel_time_reset.argtypes = [P]
     lib.ddlpb_kernel_time_reset.restype = C.c_int
+    lib.ddlpb_energy_noalloc.argtypes = [C.c_int, C.c_int, P, P, P, P]
+    lib.ddlpb_energy_noalloc.restype = C.c_int
+    lib.ddlpb_noalloc_last_error.argtypes = []
+    lib.ddlpb_noalloc_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -111,6 +115,17 @@ def _ptr(a):
         return a.ctypes.data_as(C.c_void_p)
     assert a.is_contiguous()
     return C.c_void_p(a.data_ptr())
+
+
+def energy_noalloc(n, lmax, charges_dev, X_dev, stream=None) -> float:
+    """E_s from device buffers through the allocation-free entry point (see include/ddlpb.h)."""
+    lib = library()
+    e = np.zeros(1)
+    st = lib.ddlpb_energy_noalloc(int(n), int(lmax), _ptr(charges_dev), _ptr(X_dev), _ptr(e),
+                                  C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise DDLPBError(st, lib.ddlpb_noalloc_last_error().decode())
+    return float(e[0])
 
 
 class Context:
