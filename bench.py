@@ -38,6 +38,7 @@ FP32_PEAK_TFLOPS_AT_MAX_CLOCK = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 la
 #   per (hit, basis function) for the A/B kernels (two bases, 8 flops each),
 #   per (target, source, basis function) for the Yukawa kernels.
 FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8}
+HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
 # dram bytes per launch from the committed ncu capture (profiles/), keyed by kernel, with the
 # source file digest they were taken on; null when the kernel source has changed since.
 NCU_TRAFFIC = {}
@@ -274,20 +275,31 @@ def main():
              "yukawa_pot": info["n_external"] * info["n_sources"] * nb,
              "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
     roofline = None
+    L = w["lmax"]
+    # The FP32 sparse blocks stream a stored basis (HBM-bound): algorithmic bytes per hit are
+    # the basis row (nb + lmax + 1 floats) plus the hit's indices (8 B forward, 12 B transpose).
+    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8),
+                    "ab_transpose_f32": info["n_hits"] * ((nb + L + 1) * 4 + 12)}
     if kstats:
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]
         base = top.rsplit("_", 1)[0]
-        flops_per_launch = units[base] * FLOPS_PER_UNIT[base]
-        achieved = flops_per_launch / (ms / n / 1e3) / 1e12
-        peak = FP32_PEAK_TFLOPS_AT_MAX_CLOCK if top.endswith("f32") else 1.25
         tr = NCU_TRAFFIC.get(top)
         traffic = tr["bytes_per_launch"] if tr and tr.get("digest") == source_digest() else None
-        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic, "launches_per_step": n / len(times),
-                    "ms_per_launch": ms / n, "share_of_step": ms / sum(times),
-                    "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if top.endswith("f32")
-                                    else "FP64 nominal 1.25 TFLOP/s")}
+        common = {"kernel": top, "traffic": traffic, "launches_per_step": n / len(times), "ms_per_launch": ms / n,
+                  "share_of_step": ms / sum(times)}
+        if top in stored_bytes:
+            achieved = stored_bytes[top] / (ms / n / 1e3) / 1e9
+            roofline = dict(bound="hbm", achieved=achieved, peak=HBM_PEAK_GBS, unit="GB/s",
+                            frac=achieved / HBM_PEAK_GBS, peak_source="measured copy bandwidth", **common)
+        else:
+            flops_per_launch = units[base] * FLOPS_PER_UNIT[base]
+            achieved = flops_per_launch / (ms / n / 1e3) / 1e12
+            peak = FP32_PEAK_TFLOPS_AT_MAX_CLOCK if top.endswith("f32") else 1.25
+            roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                            peak_source=("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz" if top.endswith("f32")
+                                         else "FP64 nominal 1.25 TFLOP/s"), **common)
+        roofline["all_kernels"] = {k: {"launches": v[0], "ms": round(v[1], 2)} for k, v in kstats.items()}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         atoms = 12

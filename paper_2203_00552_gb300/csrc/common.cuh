@@ -63,6 +63,13 @@ struct OpSet {
     T* extA = nullptr;      // [E] scratch
     T* gridA = nullptr;     // [M*N] scratch
     T* gridB = nullptr;     // [M*N] scratch
+    // stored basis of the sparse blocks (FP32 set only)
+    bool stored = false;
+    int nbp = 0;            // nb rounded up to a multiple of 32
+    T* Bp = nullptr;        // [nb][H]   omega r^l Y, point-major hit order
+    T* Rp = nullptr;        // [L+1][H]  i-ratio corrections
+    T* Bt = nullptr;        // [H][nbp]  same values in the transposed (target-major) hit order
+    T* Rt = nullptr;        // [H][L+1]
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -116,6 +123,8 @@ struct ddlpb_ctx {
     int* hit_ptr = nullptr;     // [M*N+1]
     int* hit_j = nullptr;       // [H]
     double* hit_w = nullptr;    // [H] omega_ij^eta(x_i^n)
+    int* hit_p = nullptr;       // [H] point index i*N+n of the hit
+    unsigned short* hit_s = nullptr;  // [H] slot of j in the neighbour list of i
     int* thit_ptr = nullptr;    // [M+1] hits grouped by the sphere j they point at
     int* thit_p = nullptr;      // [H] point index i*N+n
     int* thit_h = nullptr;      // [H] index of the hit in the point-major list

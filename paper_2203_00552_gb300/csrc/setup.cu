@@ -118,7 +118,8 @@ __global__ void k_grid_switch(int M, int N, double eta, const double4* __restric
 
 __global__ void k_hits_fill(int M, int N, double eta, const double4* __restrict__ sph, const double4* __restrict__ leb,
                             const int* __restrict__ nptr, const int* __restrict__ nidx, const double* __restrict__ fval,
-                            const int* __restrict__ hptr, int* __restrict__ hj, double* __restrict__ hw) {
+                            const int* __restrict__ hptr, int* __restrict__ hj, double* __restrict__ hw,
+                            int* __restrict__ hp, unsigned short* __restrict__ hs) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long long)M * N) return;
     int i = (int)(p / N), n = (int)(p % N);
@@ -135,39 +136,37 @@ __global__ void k_hits_fill(int M, int N, double eta, const double4* __restrict_
         if (t < 1.0) {
             hj[o] = j;
             hw[o] = d * chi_eta(t, eta);
+            hp[o] = (int)p;
+            hs[o] = (unsigned short)(k - nptr[i]);
             ++o;
         }
     }
 }
 
-// Hits grouped by their target sphere j: for every i in N_j (N is symmetric),
-// every point of sphere i whose hit list contains j.  Deterministic order.
-__global__ void k_thits(int M, int N, const int* __restrict__ nptr, const int* __restrict__ nidx,
-                        const int* __restrict__ hptr, const int* __restrict__ hj, const double* __restrict__ hw,
-                        const int* __restrict__ tptr, int* __restrict__ tcnt, int* __restrict__ tp,
-                        int* __restrict__ th, double* __restrict__ tw) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= M) return;
-    int c = 0;
-    int o = tptr ? tptr[j] : 0;
-    for (int k = nptr[j]; k < nptr[j + 1]; ++k) {
-        int i = nidx[k];
-        for (int n = 0; n < N; ++n) {
-            long long p = (long long)i * N + n;
-            for (int h = hptr[p]; h < hptr[p + 1]; ++h) {
-                if (hj[h] == j) {
-                    if (tptr) {
-                        tp[o] = (int)p;
-                        th[o] = h;
-                        tw[o] = hw[h];
-                        ++o;
-                    }
-                    ++c;
-                }
-            }
-        }
+// Transposed hit list: the hits sorted (stably) by their target sphere j, so that within
+// each j the points stay in point-major order.  Filled from the sorted hit indices.
+__global__ void k_iota(int n, int* __restrict__ v) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) v[k] = k;
+}
+
+__global__ void k_thits_gather(int H, const int* __restrict__ order, const int* __restrict__ hp,
+                               const double* __restrict__ hw, int* __restrict__ tp, double* __restrict__ tw) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < H) {
+        int h = order[k];
+        tp[k] = hp[h];
+        tw[k] = hw[h];
     }
-    if (!tptr) tcnt[j] = c;
+}
+
+// thit_ptr[j] = first position of key j in the sorted keys (keys are sphere indices).
+__global__ void k_segment_starts(int H, int M, const int* __restrict__ keys, int* __restrict__ ptr) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > H) return;
+    int cur = k < H ? keys[k] : M;
+    int prev = k > 0 ? keys[k - 1] : -1;
+    for (int j = prev + 1; j <= cur; ++j) ptr[j] = k;
 }
 
 __global__ void k_ext_fill(int M, int N, const double4* __restrict__ sph, const double4* __restrict__ leb,
@@ -402,25 +401,39 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
     c->H = H;
     DDLPB_TRY(ctx_alloc(c, &c->hit_j, H));
     DDLPB_TRY(ctx_alloc(c, &c->hit_w, H));
+    DDLPB_TRY(ctx_alloc(c, &c->hit_p, H));
+    DDLPB_TRY(ctx_alloc(c, &c->hit_s, H));
     k_hits_fill<<<ceil_div(MN, 256), 256, 0, st>>>(M, N, c->eta, c->sph, c->leb, c->nbr_ptr, c->nbr_idx, c->fval,
-                                                   c->hit_ptr, c->hit_j, c->hit_w);
+                                                   c->hit_ptr, c->hit_j, c->hit_w, c->hit_p, c->hit_s);
     DDLPB_LAUNCHED(c, "hits_fill");
 
-    // -- transposed hits
-    int* tcnt = nullptr;
-    DDLPB_TRY(ctx_alloc(c, &tcnt, M + 1));
-    DDLPB_CK(c, cudaMemsetAsync(tcnt, 0, sizeof(int) * (M + 1), st));
-    k_thits<<<ceil_div(M, 64), 64, 0, st>>>(M, N, c->nbr_ptr, c->nbr_idx, c->hit_ptr, c->hit_j, c->hit_w, nullptr,
-                                            tcnt, nullptr, nullptr, nullptr);
-    DDLPB_LAUNCHED(c, "thits_count");
+    // -- transposed hits (stable radix sort of the hit indices by target sphere)
     DDLPB_TRY(ctx_alloc(c, &c->thit_ptr, M + 1));
-    DDLPB_TRY(scan_exclusive(c, tcnt, c->thit_ptr, M + 1));
     DDLPB_TRY(ctx_alloc(c, &c->thit_p, H));
     DDLPB_TRY(ctx_alloc(c, &c->thit_w, H));
     DDLPB_TRY(ctx_alloc(c, &c->thit_h, H));
-    k_thits<<<ceil_div(M, 64), 64, 0, st>>>(M, N, c->nbr_ptr, c->nbr_idx, c->hit_ptr, c->hit_j, c->hit_w,
-                                            c->thit_ptr, tcnt, c->thit_p, c->thit_h, c->thit_w);
-    DDLPB_LAUNCHED(c, "thits_fill");
+    {
+        int *keys_out = nullptr, *vals_in = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &keys_out, H));
+        DDLPB_TRY(ctx_alloc(c, &vals_in, H));
+        if (H > 0) {
+            k_iota<<<ceil_div(H, 256), 256, 0, st>>>(H, vals_in);
+            DDLPB_LAUNCHED(c, "iota");
+            size_t bytes = 0;
+            int bits = 1;
+            while ((1 << bits) < M + 1) ++bits;
+            DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(nullptr, bytes, c->hit_j, keys_out, vals_in, c->thit_h, H, 0,
+                                                        bits, st));
+            void* tmp = nullptr;
+            DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+            DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(tmp, bytes, c->hit_j, keys_out, vals_in, c->thit_h, H, 0, bits,
+                                                        st));
+            k_thits_gather<<<ceil_div(H, 256), 256, 0, st>>>(H, c->thit_h, c->hit_p, c->hit_w, c->thit_p, c->thit_w);
+            DDLPB_LAUNCHED(c, "thits_gather");
+        }
+        k_segment_starts<<<ceil_div(H + 1, 256), 256, 0, st>>>(H, M, keys_out, c->thit_ptr);
+        DDLPB_LAUNCHED(c, "segment_starts");
+    }
 
     // -- external points (chi_i^eta > 0) and the spheres that own them
     DDLPB_TRY(scan_exclusive(c, isext, epos, MN + 1));
