@@ -193,10 +193,17 @@ def main():
                         surface=w["surface"], stream=stream.cuda_stream, **opts)
         x = torch.randn(ctx.nvec, dtype=torch.float64, device=dev)
         y = torch.empty_like(x)
-        for op in (10, 11, 12, 13):
+        times = {}
+        for op, name in ((10, "AB32"), (11, "ABT32"), (12, "C32"), (13, "CT32"), (2, "AB64"), (4, "C64")):
             ctx.apply(op, x, y)
-        torch.cuda.synchronize()
-        print(json.dumps({"ops_only": args.workload, "info": ctx.info()}), flush=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                ctx.apply(op, x, y)
+            torch.cuda.synchronize()
+            times[name] = (time.perf_counter() - t0) / reps * 1e3
+        print(json.dumps({"ops_only": args.workload, "ms_per_apply": times, "info": ctx.info()}), flush=True)
         ctx.close()
         return
 

@@ -235,12 +235,16 @@ __global__ void k_inverse_perm(int H, const int* __restrict__ order, int* __rest
 }
 
 // y = [A x_r ; B x_e] from the stored basis: one CTA per sphere i, one thread per hit,
-// grid values accumulated per point in shared memory, then projected.
+// grid values accumulated per point in shared memory, then projected.  The coefficient
+// loop is flat (the i-ratio changes at l^2) so that the basis loads of several (l, m)
+// are in flight at once.
 template <typename T, typename V4>
-__global__ void k_ab_apply_stored(int M, int N, int nb, int L, long long H, const V4* __restrict__ leb,
-                                  const int* __restrict__ hptr, const int* __restrict__ hp, const int* __restrict__ hj,
-                                  const T* __restrict__ Bp, const T* __restrict__ Rp, const T* __restrict__ Y,
-                                  const T* __restrict__ x, T* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_ab_apply_stored(int M, int N, int nb, int L, long long H,
+                                                         const V4* __restrict__ leb, const int* __restrict__ hptr,
+                                                         const int* __restrict__ hp, const int* __restrict__ hj,
+                                                         const T* __restrict__ Bp, const T* __restrict__ Rp,
+                                                         const T* __restrict__ Y, const T* __restrict__ x,
+                                                         T* __restrict__ y) {
     extern __shared__ unsigned char smraw[];
     T* vr = (T*)smraw;
     T* ve = vr + N;
@@ -258,17 +262,20 @@ __global__ void k_ab_apply_stored(int M, int N, int nb, int L, long long H, cons
         const int n = hp[h] - i * N, j = hj[h];
         const T* Xr = xr + (size_t)j * nb;
         const T* Xe = xe + (size_t)j * nb;
+        const T* b = Bp + h;
         T ur = 0, ue = 0;
-        int idx = 0;
-        for (int l = 0; l <= L; ++l) {
-            T sr = 0, se = 0;
-            for (int m = 0; m <= 2 * l; ++m, ++idx) {
-                T bv = Bp[(size_t)idx * H + h];
-                sr += __ldg(Xr + idx) * bv;
-                se += __ldg(Xe + idx) * bv;
+        int l = 0, lend = 1;
+        T rat = Rp[h];
+#pragma unroll 8
+        for (int idx = 0; idx < nb; ++idx) {
+            if (idx == lend) {
+                ++l;
+                lend = (l + 1) * (l + 1);
+                rat = Rp[(size_t)l * H + h];
             }
-            ur += sr;
-            ue += Rp[(size_t)l * H + h] * se;
+            T bv = b[(size_t)idx * H];
+            ur += __ldg(Xr + idx) * bv;
+            ue += __ldg(Xe + idx) * bv * rat;
         }
         atomicAdd(vr + n, ur);
         atomicAdd(ve + n, ue);
@@ -288,14 +295,17 @@ __global__ void k_ab_apply_stored(int M, int N, int nb, int L, long long H, cons
 }
 
 // y = [A^T x_r ; B^T x_e] from the stored basis: one CTA per target sphere j; each warp
-// walks the hits into j, lanes over (l, m) slots (4 per lane for nb <= 128, more above),
+// takes 32 hits into j at a time (their synthesis weights gathered by the 32 lanes at
+// once and broadcast by shuffles), then walks them with lanes over (l, m) slots,
 // accumulating in registers; zr, ze are the weighted syntheses of the two blocks.
 #define ABT_SLOTS 10
 template <typename T, typename V4>
-__global__ void k_ab_transpose_stored(int M, int nb, int nbp, int L, const int* __restrict__ tptr,
-                                      const int* __restrict__ tp, const T* __restrict__ Bt, const T* __restrict__ Rt,
-                                      const T* __restrict__ zr, const T* __restrict__ ze, const T* __restrict__ x,
-                                      T* __restrict__ y) {
+__global__ void __launch_bounds__(256) k_ab_transpose_stored(int M, int nb, int nbp, int L,
+                                                             const int* __restrict__ tptr,
+                                                             const int* __restrict__ tp, const T* __restrict__ Bt,
+                                                             const T* __restrict__ Rt, const T* __restrict__ zr,
+                                                             const T* __restrict__ ze, const T* __restrict__ x,
+                                                             T* __restrict__ y) {
     extern __shared__ unsigned char smraw[];
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
     T* accR = (T*)smraw;
@@ -312,17 +322,27 @@ __global__ void k_ab_transpose_stored(int M, int nb, int nbp, int L, const int* 
         ae[s] = 0;
     }
     const int k0 = tptr[j], k1 = tptr[j + 1];
-    for (int k = k0 + warp; k < k1; k += nw) {
-        const int p = tp[k];
-        const T a = zr[p], e = ze[p];
-        const T* row = Bt + (size_t)k * nbp;
-        const T* rat = Rt + (size_t)k * (L + 1);
+    for (int kb = k0 + warp * 32; kb < k1; kb += nw * 32) {
+        const int kk = kb + lane;
+        T al = 0, el = 0;
+        if (kk < k1) {
+            int p = tp[kk];
+            al = zr[p];
+            el = ze[p];
+        }
+        const int cnt = min(32, k1 - kb);
+#pragma unroll 2
+        for (int q = 0; q < cnt; ++q) {
+            const T a = __shfl_sync(0xffffffffu, al, q), e = __shfl_sync(0xffffffffu, el, q);
+            const T* row = Bt + (size_t)(kb + q) * nbp;
+            const T* rat = Rt + (size_t)(kb + q) * (L + 1);
 #pragma unroll
-        for (int s = 0; s < ABT_SLOTS; ++s) {
-            if (s < nslot) {
-                T bv = row[s * 32 + lane];
-                ar[s] += a * bv;
-                ae[s] += e * __ldg(rat + lof[s]) * bv;
+            for (int s = 0; s < ABT_SLOTS; ++s) {
+                if (s < nslot) {
+                    T bv = row[s * 32 + lane];
+                    ar[s] += a * bv;
+                    ae[s] += e * __ldg(rat + lof[s]) * bv;
+                }
             }
         }
     }
@@ -761,16 +781,16 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
         if (!transpose) {
             size_t smem = sizeof(T) * 2 * (size_t)c->N;
             KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
-            k_ab_apply_stored<T, V4><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, c->H, S.leb, c->hit_ptr,
+            k_ab_apply_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->N, c->nb, L, c->H, S.leb, c->hit_ptr,
                                                                      c->hit_p, c->hit_j, S.Bp, S.Rp, S.Y, x, y);
             DDLPB_LAUNCHED(c, "ab_apply_stored");
             return DDLPB_OK;
         }
         DDLPB_TRY(synthesis_T<T>(c, S, x, c->M, S.gridA, true));
         DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
-        size_t smem = sizeof(T) * 2 * (size_t)(BLK / 32) * S.nbp;
+        size_t smem = sizeof(T) * 2 * (size_t)(256 / 32) * S.nbp;
         KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
-        k_ab_transpose_stored<T, V4><<<c->M, BLK, smem, c->stream>>>(c->M, c->nb, S.nbp, L, c->thit_ptr, c->thit_p,
+        k_ab_transpose_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->nb, S.nbp, L, c->thit_ptr, c->thit_p,
                                                                      S.Bt, S.Rt, S.gridA, S.gridB, x, y);
         DDLPB_LAUNCHED(c, "ab_transpose_stored");
         return DDLPB_OK;
