@@ -283,10 +283,9 @@ def main():
              "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
     roofline = None
     L = w["lmax"]
-    # The FP32 sparse blocks stream a stored basis (HBM-bound): algorithmic bytes per hit are
-    # the basis row (nb + lmax + 1 floats) plus the hit's indices (8 B forward, 12 B transpose).
-    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8),
-                    "ab_transpose_f32": info["n_hits"] * ((nb + L + 1) * 4 + 12)}
+    # The FP32 A/B product streams a stored basis (HBM-bound): algorithmic bytes per hit are
+    # the basis row (nb + lmax + 1 floats) plus the hit's point and sphere indices (8 B).
+    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8)}
     if kstats:
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]

@@ -68,8 +68,6 @@ struct OpSet {
     int nbp = 0;            // nb rounded up to a multiple of 32
     T* Bp = nullptr;        // [nb][H]   omega r^l Y, point-major hit order
     T* Rp = nullptr;        // [L+1][H]  i-ratio corrections
-    T* Bt = nullptr;        // [H][nbp]  same values in the transposed (target-major) hit order
-    T* Rt = nullptr;        // [H][L+1]
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.

@@ -191,17 +191,16 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
 
 // ---------------------------------------------------------------- A and B, stored basis
 
-// Stored ("incore") form of the sparse blocks: for every hit h = (i, n, j) the weighted
-// basis omega_ij^eta r_l^j Y_lm^j at x_i^n and the i-ratio correction
-// rat_l = i_l(kappa rho)/i_l(kappa r_j) / (rho/r_j)^l are computed once at setup.
-// Bp is coefficient-major [lm][H] (threads over hits read consecutive addresses),
-// Bt is hit-major in the transposed order [k][nbp] with rows padded to nbp = 32k.
+// Stored ("incore", Sec. 4) form of the sparse blocks A and B: for every hit h = (i, n, j)
+// the weighted basis omega_ij^eta r_l^j Y_lm^j at x_i^n and the i-ratio correction
+// rat_l = i_l(kappa rho)/i_l(kappa r_j) / (rho/r_j)^l are computed once at setup, in
+// coefficient-major layout [lm][H] (threads over hits read consecutive addresses).  The
+// transposes keep evaluating the basis on the fly (measured faster for the gather).
 template <typename T, typename V4>
-__global__ void k_ab_store(int H, int N, int nb, int nbp, int L, T kappa, const V4* __restrict__ sph,
+__global__ void k_ab_store(int H, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
                            const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ hp,
                            const int* __restrict__ hj, const T* __restrict__ hw, const T* __restrict__ Sinv,
-                           const int* __restrict__ tpos, T* __restrict__ Bp, T* __restrict__ Rp, T* __restrict__ Bt,
-                           T* __restrict__ Rt) {
+                           T* __restrict__ Bp, T* __restrict__ Rp) {
     extern __shared__ unsigned char smraw[];
     T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x;
@@ -216,22 +215,9 @@ __global__ void k_ab_store(int H, int N, int nb, int nbp, int L, T kappa, const 
     const T w = hw[h];
     radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
     radial<T>(1, L, rho, b.w, kappa, Sinv + (size_t)j * (L + 2), ri + tid, nullptr, bd);
-    const long long k = tpos[h];
-    for (int l = 0; l <= L; ++l) {
-        T r = ri[tid + l * bd] / rr[tid + l * bd];
-        Rp[(size_t)l * H + h] = r;
-        Rt[(size_t)k * (L + 1) + l] = r;
-    }
-    ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
-        T v = w * rr[tid + l * bd] * yv;
-        Bp[(size_t)idx * H + h] = v;
-        Bt[(size_t)k * nbp + idx] = v;
-    });
-}
-
-__global__ void k_inverse_perm(int H, const int* __restrict__ order, int* __restrict__ pos) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < H) pos[order[k]] = k;
+    for (int l = 0; l <= L; ++l) Rp[(size_t)l * H + h] = ri[tid + l * bd] / rr[tid + l * bd];
+    ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
+                  [&](int idx, int l, T yv) { Bp[(size_t)idx * H + h] = w * rr[tid + l * bd] * yv; });
 }
 
 // y = [A x_r ; B x_e] from the stored basis: one CTA per sphere i, one thread per hit,
@@ -291,78 +277,6 @@ __global__ void __launch_bounds__(256) k_ab_apply_stored(int M, int N, int nb, i
         size_t o = (size_t)i * nb + idx;
         y[o] = xr[o] - ar;
         y[(size_t)M * nb + o] = xe[o] - ae;
-    }
-}
-
-// y = [A^T x_r ; B^T x_e] from the stored basis: one CTA per target sphere j; each warp
-// takes 32 hits into j at a time (their synthesis weights gathered by the 32 lanes at
-// once and broadcast by shuffles), then walks them with lanes over (l, m) slots,
-// accumulating in registers; zr, ze are the weighted syntheses of the two blocks.
-#define ABT_SLOTS 10
-template <typename T, typename V4>
-__global__ void __launch_bounds__(256) k_ab_transpose_stored(int M, int nb, int nbp, int L,
-                                                             const int* __restrict__ tptr,
-                                                             const int* __restrict__ tp, const T* __restrict__ Bt,
-                                                             const T* __restrict__ Rt, const T* __restrict__ zr,
-                                                             const T* __restrict__ ze, const T* __restrict__ x,
-                                                             T* __restrict__ y) {
-    extern __shared__ unsigned char smraw[];
-    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
-    T* accR = (T*)smraw;
-    T* accE = accR + nw * nbp;
-    const int j = blockIdx.x;
-    const int nslot = nbp >> 5;
-    int lof[ABT_SLOTS];
-    T ar[ABT_SLOTS], ae[ABT_SLOTS];
-#pragma unroll
-    for (int s = 0; s < ABT_SLOTS; ++s) {
-        int idx = s * 32 + lane;
-        lof[s] = idx < nb ? (int)sqrtf((float)idx + 0.5f) : 0;
-        ar[s] = 0;
-        ae[s] = 0;
-    }
-    const int k0 = tptr[j], k1 = tptr[j + 1];
-    for (int kb = k0 + warp * 32; kb < k1; kb += nw * 32) {
-        const int kk = kb + lane;
-        T al = 0, el = 0;
-        if (kk < k1) {
-            int p = tp[kk];
-            al = zr[p];
-            el = ze[p];
-        }
-        const int cnt = min(32, k1 - kb);
-#pragma unroll 2
-        for (int q = 0; q < cnt; ++q) {
-            const T a = __shfl_sync(0xffffffffu, al, q), e = __shfl_sync(0xffffffffu, el, q);
-            const T* row = Bt + (size_t)(kb + q) * nbp;
-            const T* rat = Rt + (size_t)(kb + q) * (L + 1);
-#pragma unroll
-            for (int s = 0; s < ABT_SLOTS; ++s) {
-                if (s < nslot) {
-                    T bv = row[s * 32 + lane];
-                    ar[s] += a * bv;
-                    ae[s] += e * __ldg(rat + lof[s]) * bv;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < ABT_SLOTS; ++s) {
-        if (s < nslot) {
-            accR[warp * nbp + s * 32 + lane] = ar[s];
-            accE[warp * nbp + s * 32 + lane] = ae[s];
-        }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nb; idx += bd) {
-        T sr = 0, se = 0;
-        for (int w = 0; w < nw; ++w) {
-            sr += accR[w * nbp + idx];
-            se += accE[w * nbp + idx];
-        }
-        size_t o = (size_t)j * nb + idx;
-        y[o] = x[o] - sr;
-        y[(size_t)M * nb + o] = x[(size_t)M * nb + o] - se;
     }
 }
 
@@ -733,20 +647,13 @@ ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
     // stored basis of the sparse blocks (FP32, two layouts)
     const long long H = c->H;
     S.nbp = ((nb + 31) / 32) * 32;
-    if (H > 0 && S.nbp / 32 <= ABT_SLOTS) {
-        int* tpos = nullptr;
-        DDLPB_TRY(ctx_alloc(c, &tpos, H));
-        k_inverse_perm<<<ceil_div(H, 256), 256, 0, c->stream>>>((int)H, c->thit_h, tpos);
-        DDLPB_LAUNCHED(c, "inverse_perm");
+    if (H > 0) {
         DDLPB_TRY(ctx_alloc(c, &S.Bp, (size_t)nb * H));
         DDLPB_TRY(ctx_alloc(c, &S.Rp, (size_t)(L + 1) * H));
-        DDLPB_TRY(ctx_alloc(c, &S.Bt, (size_t)S.nbp * H));
-        DDLPB_TRY(ctx_alloc(c, &S.Rt, (size_t)(L + 1) * H));
-        DDLPB_CK(c, cudaMemsetAsync(S.Bt, 0, sizeof(float) * S.nbp * H, c->stream));
         size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
-        k_ab_store<float><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, S.nbp, L, (float)c->kappa, S.sph,
-                                                                      S.leb, S.yt, c->hit_p, c->hit_j, S.hit_w,
-                                                                      S.Sinv, tpos, S.Bp, S.Rp, S.Bt, S.Rt);
+        k_ab_store<float><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, L, (float)c->kappa, S.sph, S.leb,
+                                                                      S.yt, c->hit_p, c->hit_j, S.hit_w, S.Sinv, S.Bp,
+                                                                      S.Rp);
         DDLPB_LAUNCHED(c, "ab_store");
         S.stored = true;
     }
@@ -776,9 +683,9 @@ template <typename T>
 ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE) {
     DDLPB_TRY(opset_prepare<T>(c, S));
     const int L = c->lmax;
-    if (S.stored && !gridR && y) {
+    if (S.stored && !gridR && y && !transpose) {
         using V4 = typename OpSet<T>::V4;
-        if (!transpose) {
+        {
             size_t smem = sizeof(T) * 2 * (size_t)c->N;
             KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
             k_ab_apply_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->N, c->nb, L, c->H, S.leb, c->hit_ptr,
@@ -786,14 +693,6 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
             DDLPB_LAUNCHED(c, "ab_apply_stored");
             return DDLPB_OK;
         }
-        DDLPB_TRY(synthesis_T<T>(c, S, x, c->M, S.gridA, true));
-        DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
-        size_t smem = sizeof(T) * 2 * (size_t)(256 / 32) * S.nbp;
-        KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
-        k_ab_transpose_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->nb, S.nbp, L, c->thit_ptr, c->thit_p,
-                                                                     S.Bt, S.Rt, S.gridA, S.gridB, x, y);
-        DDLPB_LAUNCHED(c, "ab_transpose_stored");
-        return DDLPB_OK;
     }
     if (!transpose) {
         size_t smem = sizeof(T) * (2 * (size_t)c->N + 2 * (size_t)(L + 1) * BLK);
