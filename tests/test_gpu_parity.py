@@ -227,3 +227,27 @@ def test_fp32_operators_track_fp64(case, op):
     ctx.apply(op + 8, x, y32)
     scale = float(y64.abs().max())
     assert float((y64 - y32).abs().max()) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gpu_kirkwood_tanford(precision):
+    """The GPU path reproduces the Kirkwood-Tanford multipole energy and force of an
+    off-centre charge (tiny charged sphere buried in a neutral one), FP64 and mixed."""
+    from scipy import special
+    a, eps2, kap, lmax = 6.0, 78.54, 0.09, 6
+    d = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    b = 0.25 * a
+    c = np.array([[0.0, 0.0, 0.0], b * d])
+    ctx = G.Context(c, np.array([a, 0.2 * a]), np.array([0.0, 0.7]), eps2, kap, lmax, 302, tol=1e-12,
+                    precision=precision)
+    ctx.solve()
+    ctx.adjoint()
+    E, F = ctx.energy(), ctx.forces()
+    Eref = dE = 0.0
+    for l in range(lmax + 1):
+        beta = kap * special.spherical_kn(l, kap * a, derivative=True) / special.spherical_kn(l, kap * a)
+        R = ((l + 1) / (eps2 * a) + beta) / (l / (eps2 * a) - beta)
+        Eref += 0.49 / 2 * R * b ** (2 * l) / a ** (2 * l + 1)
+        dE += 0.49 / 2 * R * 2 * l * b ** (2 * l - 1) / a ** (2 * l + 1) if l else 0.0
+    assert abs(E - Eref) <= 1e-10 * abs(Eref)
+    assert np.allclose(F[1], -dE * d, rtol=1e-8, atol=1e-12)

@@ -242,3 +242,41 @@ def test_rotation_fluctuation_shrinks_with_discretisation():
             Es.append(E)
         spreads.append(np.ptp(Es))
     assert spreads[1] < spreads[0]
+
+
+def _kirkwood_tanford(q, a, b, eps2, kappa, lmax, eps1=1.0):
+    """Energy and radial force of a charge q at distance b from the centre of a dielectric
+    ball of radius a (eps1 inside) in a screened solvent (eps2, kappa), truncated at lmax:
+    E = q^2/(2 eps1) sum_l R_l b^(2l) / a^(2l+1),
+    R_l = [(eps1/eps2)(l+1)/a + beta_l] / [(eps1/eps2) l/a - beta_l], beta_l = kappa k_l'(kappa a)/k_l(kappa a)."""
+    E = 0.0
+    dE = 0.0
+    for l in range(lmax + 1):
+        beta = kappa * special.spherical_kn(l, kappa * a, derivative=True) / special.spherical_kn(l, kappa * a)
+        R = ((eps1 / eps2) * (l + 1) / a + beta) / ((eps1 / eps2) * l / a - beta)
+        E += R * b ** (2 * l) / a ** (2 * l + 1)
+        if l > 0:
+            dE += R * 2 * l * b ** (2 * l - 1) / a ** (2 * l + 1)
+    return q * q / (2 * eps1) * E, q * q / (2 * eps1) * dE
+
+
+@pytest.mark.parametrize("lmax,n", [(3, 110), (6, 302)])  # quadrature degree >= lmax + 14: aliasing < 1e-12
+def test_kirkwood_tanford_off_centre_charge(lmax, n):
+    """A charged atom with a tiny sphere buried inside a large neutral sphere: the large sphere
+    behaves as an isolated dielectric ball and the small one samples its reaction field at the
+    charge, so the discrete energy equals the Kirkwood-Tanford multipole sum up to lmax (this pins
+    every l > 0 factor of C1, C2, F0 and the A coupling) and the analytical force equals -dE/db."""
+    a, eps2, kap = 6.0, 78.54, 0.09
+    b_dir = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    b = 0.25 * a
+    c = np.array([[0.0, 0.0, 0.0], b * b_dir])
+    r = np.array([a, 0.2 * a])
+    q = np.array([0.0, 0.7])
+    E, F, p = O.run(c, r, q, eps2, kap, lmax, n)
+    E_ref, dE_ref = _kirkwood_tanford(0.7, a, b, eps2, kap, lmax)
+    assert abs(E - E_ref) <= 1e-10 * abs(E_ref)
+    assert np.allclose(F[1], -dE_ref * b_dir, rtol=1e-8, atol=1e-12)
+    assert np.allclose(F[0], -F[1], rtol=1e-10, atol=1e-14)
+    # the l > 0 terms matter: dropping them changes the energy well beyond the tolerance
+    E0, _ = _kirkwood_tanford(0.7, a, b, eps2, kap, 0)
+    assert abs(E_ref - E0) > 1e-4 * abs(E_ref)
