@@ -160,9 +160,17 @@ class DDLPB:
     def _switch(self):
         M, N = self.M, self.N
         self.f = np.zeros((M, N))
+        self.Z = np.zeros((M, N, 3))
         for i in range(M):
-            for j in self.nbrs[i]:
-                self.f[i] += chi_eta(self.t(i, j), self.eta)
+            js = self.nbrs[i]
+            if len(js) == 0:
+                continue
+            d = self.pts[i][:, None, :] - self.x[js][None, :, :]        # [N, k, 3]
+            dist = np.linalg.norm(d, axis=2)
+            t = dist / self.r[js][None, :]                              # r_1^j(x_i^n)
+            self.f[i] = chi_eta(t, self.eta).sum(1)
+            # Z_n^i = sum_{k0 in N_i} chi'(r_1^k0) e^k0 / r_k0
+            self.Z[i] = ((dchi_eta(t, self.eta) / self.r[js][None, :])[:, :, None] * d / dist[:, :, None]).sum(1)
         f = self.f
         self.d = np.where(f > 1.0, 1.0 / np.where(f > 1.0, f, 1.0), 1.0)
         # chi_i^eta = 1 - sum_j omega_ij = 1 - d f, which Sec. 3.1 (below Eq.
@@ -170,11 +178,6 @@ class DDLPB:
         # rounding residue of 1 - (1/f) f survives there
         self.chi = np.where(f >= 1.0, 0.0, 1.0 - self.d * f)
         self.delta_gt1 = (f > 1.0).astype(np.float64)
-        # Z_n^i = sum_{k0 in N_i} chi'(r_1^k0) e^k0 / r_k0
-        self.Z = np.zeros((M, N, 3))
-        for i in range(M):
-            for j in self.nbrs[i]:
-                self.Z[i] += (dchi_eta(self.t(i, j), self.eta) / self.r[j])[:, None] * self.e(i, j)
 
     def omega(self, i, j):
         """omega_ij^eta(x_i^n) over n (Eq. regular_omega_ij)."""
@@ -246,6 +249,33 @@ class DDLPB:
                 v += self.omega(i, j) * (self.basis(kind, j, self.pts[i]) @ Xr[j])
             out[i] -= self.analysis(v)
         return out
+
+    def apply_A_rows(self, Xc, rows, kind="r"):
+        """Rows `rows` of A X (kind 'r') or B X (kind 'i'), for sampled checks at full size."""
+        out = []
+        for i in rows:
+            v = np.zeros(self.N)
+            for j in self.nbrs[i]:
+                v += self.omega(i, j) * (self.basis(kind, j, self.pts[i]) @ Xc[j])
+            out.append(Xc[i] - self.analysis(v))
+        return np.array(out)
+
+    def apply_K_rows(self, y, rows):
+        """Rows `rows` of apply_K(y) (all sources, sampled targets)."""
+        src = [j for j in range(self.M) if np.any(self.chi[j] > 0)]
+        mu = np.zeros((self.M, self.nb))
+        for j in src:   # P chi_j = 0 on spheres without external points
+            mu[j] = self.lexpand(self.cik[j]) * (self._pchi(j) @ y[j])
+        out = []
+        for i in rows:
+            ext = self.chi[i] > 0
+            phi = np.zeros(self.N)
+            if ext.any():
+                P = self.pts[i][ext]
+                for j in src:
+                    phi[ext] += self.basis("k", j, P) @ mu[j]
+            out.append(self.analysis(self.chi[i] * phi))
+        return np.array(out)
 
     def apply_B(self, Xe):
         return self.apply_A(Xe, kind="i")
