@@ -39,8 +39,8 @@ FP32_PEAK_TFLOPS_AT_MAX_CLOCK = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 la
 #   per (target, source, basis function) for the Yukawa kernels.
 FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8}
 HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
-# dram bytes per launch from the committed ncu capture (profiles/), keyed by kernel, with the
-# source file digest they were taken on; null when the kernel source has changed since.
+# dram bytes per launch from the committed ncu capture (profiles/), keyed by (kernel, workload),
+# with the digest of the operator sources they were taken on; null once those sources change.
 NCU_TRAFFIC = {}
 
 
@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--restart", type=int, default=300)
-    ap.add_argument("--precond-tol", type=float, default=1e-1)
+    ap.add_argument("--precond-tol", type=float, default=0.4)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
@@ -290,7 +290,7 @@ def main():
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]
         base = top.rsplit("_", 1)[0]
-        tr = NCU_TRAFFIC.get(top)
+        tr = NCU_TRAFFIC.get((top, args.workload))
         traffic = tr["bytes_per_launch"] if tr and tr.get("digest") == source_digest() else None
         common = {"kernel": top, "traffic": traffic, "launches_per_step": n / len(times), "ms_per_launch": ms / n,
                   "share_of_step": ms / sum(times)}

@@ -267,6 +267,48 @@ __device__ __forceinline__ void ylm_stream(int lmax, T x, T y, T z, const YTabT<
     }
 }
 
+// Stream Y_lm at two unit vectors u0, u1 at once, calling f(idx, l, Y(u0), Y(u1)).
+template <typename T, typename F>
+__device__ __forceinline__ void ylm_stream2(int lmax, T x0, T y0, T z0, T x1, T y1, T z1, const YTabT<T>& yt,
+                                            F&& f) {
+    const T SQ2 = (T)1.4142135623730951;
+    T cr0 = 1, ci0 = 0, cr1 = 1, ci1 = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        if (m > 0) {
+            T n0 = cr0 * x0 - ci0 * y0;
+            ci0 = cr0 * y0 + ci0 * x0;
+            cr0 = n0;
+            T n1 = cr1 * x1 - ci1 * y1;
+            ci1 = cr1 * y1 + ci1 * x1;
+            cr1 = n1;
+        }
+        const T qmm = (T)__ldg(yt.qmm + m);
+        T p0 = qmm, p1 = qmm;
+        const T sr0 = SQ2 * cr0, si0 = SQ2 * ci0, sr1 = SQ2 * cr1, si1 = SQ2 * ci1;
+        if (m == 0) {
+            f(0, 0, p0, p1);
+        } else {
+            f(m * m + 2 * m, m, p0 * sr0, p1 * sr1);
+            f(m * m, m, p0 * si0, p1 * si1);
+        }
+        if (m + 1 <= lmax) {
+            const T c1 = (T)__ldg(yt.q1 + m);
+            T q0 = c1 * z0 * p0, q1 = c1 * z1 * p1;
+            int l = m + 1;
+            if (m == 0) f(l * l + l, l, q0, q1);
+            else { f(l * l + l + m, l, q0 * sr0, q1 * sr1); f(l * l + l - m, l, q0 * si0, q1 * si1); }
+            for (l = m + 2; l <= lmax; ++l) {
+                const T a = (T)__ldg(yt.a + l * DDLPB_LT + m), bb = (T)__ldg(yt.b + l * DDLPB_LT + m);
+                T r0 = a * (z0 * q0 - bb * p0), r1 = a * (z1 * q1 - bb * p1);
+                p0 = q0; q0 = r0;
+                p1 = q1; q1 = r1;
+                if (m == 0) f(l * l + l, l, r0, r1);
+                else { f(l * l + l + m, l, r0 * sr0, r1 * sr1); f(l * l + l - m, l, r0 * si0, r1 * si1); }
+            }
+        }
+    }
+}
+
 // Stream Y_lm(u) and the ambient gradient G of F(x,y,z) = Q_l^m(z) C_m(x,y),
 // whose tangential projection G - (u.G) u is the surface gradient of Y_lm at u
 // (used for Eq. derivative_ylm).  Calls f(idx, l, Y, Gx, Gy, Gz).

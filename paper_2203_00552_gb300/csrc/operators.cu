@@ -142,7 +142,7 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
     T* accR = sm;
     T* accE = accR + nw * nb;
-    T* rr = accE + nw * nb;
+    T* rr = accE + nw * nb;          // rr | ri | rr (second hit) | ri (second hit), (L+1)*bd each
     T* ri = rr + (L + 1) * bd;
     const int j = blockIdx.x;
     const V4 b = sph[j];
@@ -150,31 +150,46 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
     __syncthreads();
     const int t0 = tptr[j], cnt = tptr[j + 1] - t0;
     const T* sinv = Sinv + (size_t)j * (L + 2);
-    for (int base = 0; base < cnt; base += bd) {
-        int h = base + tid;
-        T dx = b.w, dy = 0, dz = 0, wr = 0, we = 0;
-        if (h < cnt) {
-            int p = tp[t0 + h];
-            int i = p / N, n = p % N;
-            V4 a = sph[i], s = leb[n];
-            dx = a.x + a.w * s.x - b.x;
-            dy = a.y + a.w * s.y - b.y;
-            dz = a.z + a.w * s.z - b.z;
-            T w = tw[t0 + h];
-            wr = w * zr[p];
-            we = w * ze[p];
-        }
-        T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
-        radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
-        radial<T>(1, L, rho, b.w, kappa, sinv, ri + tid, nullptr, bd);
-        ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
-            T vR = warp_sum(wr * rr[tid + l * bd] * yv);
-            T vE = warp_sum(we * ri[tid + l * bd] * yv);
-            if (lane == 0) {
-                accR[warp * nb + idx] += vR;
-                accE[warp * nb + idx] += vE;
+    // two hits per thread (base + tid and base + bd + tid), summed before each warp reduction
+    for (int base = 0; base < cnt; base += 2 * bd) {
+        T dx[2], dy[2], dz[2], wr[2], we[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            int h = base + u * bd + tid;
+            dx[u] = b.w; dy[u] = 0; dz[u] = 0; wr[u] = 0; we[u] = 0;
+            if (h < cnt) {
+                int p = tp[t0 + h];
+                int i = p / N, n = p % N;
+                V4 a = sph[i], s = leb[n];
+                dx[u] = a.x + a.w * s.x - b.x;
+                dy[u] = a.y + a.w * s.y - b.y;
+                dz[u] = a.z + a.w * s.z - b.z;
+                T w = tw[t0 + h];
+                wr[u] = w * zr[p];
+                we[u] = w * ze[p];
             }
-        });
+        }
+        T e[2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            T rho = sqrt(dx[u] * dx[u] + dy[u] * dy[u] + dz[u] * dz[u]), inv = (T)1 / rho;
+            radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid + u * (L + 1) * bd * 2, nullptr, bd);
+            radial<T>(1, L, rho, b.w, kappa, sinv, ri + tid + u * (L + 1) * bd * 2, nullptr, bd);
+            e[u][0] = dx[u] * inv;
+            e[u][1] = dy[u] * inv;
+            e[u][2] = dz[u] * inv;
+        }
+        const T* rr1 = rr + (L + 1) * bd * 2;
+        const T* ri1 = ri + (L + 1) * bd * 2;
+        ylm_stream2<T>(L, e[0][0], e[0][1], e[0][2], e[1][0], e[1][1], e[1][2], yt,
+                       [&](int idx, int l, T y0, T y1) {
+                           T vR = warp_sum(wr[0] * rr[tid + l * bd] * y0 + wr[1] * rr1[tid + l * bd] * y1);
+                           T vE = warp_sum(we[0] * ri[tid + l * bd] * y0 + we[1] * ri1[tid + l * bd] * y1);
+                           if (lane == 0) {
+                               accR[warp * nb + idx] += vR;
+                               accE[warp * nb + idx] += vE;
+                           }
+                       });
     }
     __syncthreads();
     for (int idx = tid; idx < nb; idx += bd) {
@@ -244,27 +259,40 @@ __global__ void __launch_bounds__(256) k_ab_apply_stored(int M, int N, int nb, i
     const T* xr = x;
     const T* xe = x + (size_t)M * nb;
     const int h0 = hptr[(long long)i * N], h1 = hptr[(long long)(i + 1) * N];
-    for (int h = h0 + tid; h < h1; h += bd) {
-        const int n = hp[h] - i * N, j = hj[h];
-        const T* Xr = xr + (size_t)j * nb;
-        const T* Xe = xe + (size_t)j * nb;
-        const T* b = Bp + h;
-        T ur = 0, ue = 0;
+    // two hits per thread in flight (h and h + bd) for memory-level parallelism
+    for (int ha = h0 + tid; ha < h1; ha += 2 * bd) {
+        const int hb = ha + bd;
+        const bool vb = hb < h1;
+        const int hbb = vb ? hb : ha;
+        const int na = hp[ha] - i * N, ja = hj[ha];
+        const int nbb = hp[hbb] - i * N, jb = hj[hbb];
+        const T* Xra = xr + (size_t)ja * nb;
+        const T* Xea = xe + (size_t)ja * nb;
+        const T* Xrb = xr + (size_t)jb * nb;
+        const T* Xeb = xe + (size_t)jb * nb;
+        T ura = 0, uea = 0, urb = 0, ueb = 0;
         int l = 0, lend = 1;
-        T rat = Rp[h];
-#pragma unroll 8
+        T rata = Rp[ha], ratb = Rp[hbb];
+#pragma unroll 4
         for (int idx = 0; idx < nb; ++idx) {
             if (idx == lend) {
                 ++l;
                 lend = (l + 1) * (l + 1);
-                rat = Rp[(size_t)l * H + h];
+                rata = Rp[(size_t)l * H + ha];
+                ratb = Rp[(size_t)l * H + hbb];
             }
-            T bv = b[(size_t)idx * H];
-            ur += __ldg(Xr + idx) * bv;
-            ue += __ldg(Xe + idx) * bv * rat;
+            const T ba = Bp[(size_t)idx * H + ha], bb = Bp[(size_t)idx * H + hbb];
+            ura += __ldg(Xra + idx) * ba;
+            uea += __ldg(Xea + idx) * ba * rata;
+            urb += __ldg(Xrb + idx) * bb;
+            ueb += __ldg(Xeb + idx) * bb * ratb;
         }
-        atomicAdd(vr + n, ur);
-        atomicAdd(ve + n, ue);
+        atomicAdd(vr + na, ura);
+        atomicAdd(ve + na, uea);
+        if (vb) {
+            atomicAdd(vr + nbb, urb);
+            atomicAdd(ve + nbb, ueb);
+        }
     }
     __syncthreads();
     for (int idx = tid; idx < nb; idx += bd) {
@@ -705,7 +733,7 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     }
     DDLPB_TRY(synthesis_T<T>(c, S, x, c->M, S.gridA, true));
     DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
-    size_t smem = sizeof(T) * (2 * (size_t)(BLK / 32) * c->nb + 2 * (size_t)(L + 1) * BLK);
+    size_t smem = sizeof(T) * (2 * (size_t)(BLK / 32) * c->nb + 4 * (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_ab_transpose<T, typename OpSet<T>::V4>, smem));
     KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
     k_ab_transpose<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,

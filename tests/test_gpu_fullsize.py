@@ -13,7 +13,7 @@ from paper_2203_00552_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-BENCH_OPTS = dict(gmres_restart=300, precond_tol=0.1, max_iter=4000)
+BENCH_OPTS = dict(gmres_restart=300, precond_tol=0.4, max_iter=4000)
 
 
 def _rows_check(w, rows, ops=(G.OP_AB, G.OP_C)):
