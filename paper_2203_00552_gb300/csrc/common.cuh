@@ -66,8 +66,10 @@ struct OpSet {
     // stored basis of the sparse blocks (FP32 set only)
     bool stored = false;
     int nbp = 0;            // nb rounded up to a multiple of 32
-    T* Bp = nullptr;        // [nb][H]   omega r^l Y, point-major hit order
-    T* Rp = nullptr;        // [L+1][H]  i-ratio corrections
+    T* Bp = nullptr;        // [nb][H]   omega r^l Y; within a sphere, hits ordered by (neighbour, point)
+    T* Rp = nullptr;        // [L+1][H]  i-ratio corrections, same order
+    int* hps = nullptr;     // [H] point index of the stored hit
+    int* hjs = nullptr;     // [H] neighbour sphere of the stored hit
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.

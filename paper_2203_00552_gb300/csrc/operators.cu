@@ -9,6 +9,8 @@
 //         phi = sum_j mu_j k^j Y^j at the external points (direct summation);
 //         out_i = sum_n w_n chi_i phi Y_lm(s_n), added to both block rows.
 //   The transposes follow the same data in reverse (gathers, no atomics).
+#include <cub/cub.cuh>
+
 #include "common.cuh"
 
 #define BLK 128
@@ -211,23 +213,39 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
 // rat_l = i_l(kappa rho)/i_l(kappa r_j) / (rho/r_j)^l are computed once at setup, in
 // coefficient-major layout [lm][H] (threads over hits read consecutive addresses).  The
 // transposes keep evaluating the basis on the fly (measured faster for the gather).
+// Within each sphere the stored hits are ordered by neighbour j, then point n (order[k] is
+// the hit index h stored at position k), so that the threads of a warp mostly read the same
+// neighbour's coefficients.
+__global__ void k_store_keys(int H, int N, const int* __restrict__ hp, const unsigned short* __restrict__ hs,
+                             unsigned long long* __restrict__ key, int* __restrict__ val) {
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= H) return;
+    const int p = hp[h];
+    key[h] = ((unsigned long long)(p / N) << 32) | ((unsigned long long)hs[h] << 16) | (unsigned long long)(p % N);
+    val[h] = h;
+}
+
 template <typename T, typename V4>
 __global__ void k_ab_store(int H, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
-                           const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ hp,
-                           const int* __restrict__ hj, const T* __restrict__ hw, const T* __restrict__ Sinv,
-                           T* __restrict__ Bp, T* __restrict__ Rp) {
+                           const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ order,
+                           const int* __restrict__ hp, const int* __restrict__ hj, const T* __restrict__ hw,
+                           const T* __restrict__ Sinv, T* __restrict__ Bp, T* __restrict__ Rp, int* __restrict__ hps,
+                           int* __restrict__ hjs) {
     extern __shared__ unsigned char smraw[];
     T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x;
     T* rr = sm;
     T* ri = rr + (L + 1) * bd;
-    const long long h = (long long)blockIdx.x * bd + tid;
+    const long long h = (long long)blockIdx.x * bd + tid;   // storage position
     if (h >= H) return;
-    const int p = hp[h], i = p / N, n = p % N, j = hj[h];
+    const int hh = order[h];
+    const int p = hp[hh], i = p / N, n = p % N, j = hj[hh];
+    hps[h] = p;
+    hjs[h] = j;
     const V4 a = sph[i], s = leb[n], b = sph[j];
     const T dx = a.x + a.w * s.x - b.x, dy = a.y + a.w * s.y - b.y, dz = a.z + a.w * s.z - b.z;
     const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
-    const T w = hw[h];
+    const T w = hw[hh];
     radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
     radial<T>(1, L, rho, b.w, kappa, Sinv + (size_t)j * (L + 2), ri + tid, nullptr, bd);
     for (int l = 0; l <= L; ++l) Rp[(size_t)l * H + h] = ri[tid + l * bd] / rr[tid + l * bd];
@@ -676,12 +694,27 @@ ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
     const long long H = c->H;
     S.nbp = ((nb + 31) / 32) * 32;
     if (H > 0) {
+        unsigned long long *kin = nullptr, *kout = nullptr;
+        int *vin = nullptr, *order = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &kin, H));
+        DDLPB_TRY(ctx_alloc(c, &kout, H));
+        DDLPB_TRY(ctx_alloc(c, &vin, H));
+        DDLPB_TRY(ctx_alloc(c, &order, H));
+        k_store_keys<<<ceil_div(H, 256), 256, 0, c->stream>>>((int)H, N, c->hit_p, c->hit_s, kin, vin);
+        DDLPB_LAUNCHED(c, "store_keys");
+        size_t bytes = 0;
+        DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(nullptr, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
+        void* tmp = nullptr;
+        DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+        DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(tmp, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
         DDLPB_TRY(ctx_alloc(c, &S.Bp, (size_t)nb * H));
         DDLPB_TRY(ctx_alloc(c, &S.Rp, (size_t)(L + 1) * H));
+        DDLPB_TRY(ctx_alloc(c, &S.hps, H));
+        DDLPB_TRY(ctx_alloc(c, &S.hjs, H));
         size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
         k_ab_store<float><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, L, (float)c->kappa, S.sph, S.leb,
-                                                                      S.yt, c->hit_p, c->hit_j, S.hit_w, S.Sinv, S.Bp,
-                                                                      S.Rp);
+                                                                      S.yt, order, c->hit_p, c->hit_j, S.hit_w, S.Sinv,
+                                                                      S.Bp, S.Rp, S.hps, S.hjs);
         DDLPB_LAUNCHED(c, "ab_store");
         S.stored = true;
     }
@@ -717,7 +750,7 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
             size_t smem = sizeof(T) * 2 * (size_t)c->N;
             KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
             k_ab_apply_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->N, c->nb, L, c->H, S.leb, c->hit_ptr,
-                                                                     c->hit_p, c->hit_j, S.Bp, S.Rp, S.Y, x, y);
+                                                                     S.hps, S.hjs, S.Bp, S.Rp, S.Y, x, y);
             DDLPB_LAUNCHED(c, "ab_apply_stored");
             return DDLPB_OK;
         }
