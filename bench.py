@@ -144,6 +144,19 @@ def clocks_stop(p, f, path, dev_index):
             "samples": len(sm)}
 
 
+def whole_job(atoms_per_rank, ms_local, world, dist=None, device="cpu"):
+    """Max step time over ranks and the whole-job throughput (all ranks' atoms / that time).
+    Each rank solves its own copy of the workload (replicas), so the only collective is this
+    reduction of one number; it works with any torch.distributed backend."""
+    t_max = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * atoms_per_rank / (t_max / 1e3)
+
+
 def source_digest():
     import hashlib
     h = hashlib.sha256()
@@ -246,12 +259,7 @@ def main():
     torch.cuda.synchronize()
     clocks = clocks_stop(*clk, local) if rank == 0 else None
     ms_step = sum(times) / len(times)
-    t_max = ms_step
-    if pg:
-        t = torch.tensor([ms_step], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t)
-    value = world * M / (t_max / 1e3)
+    t_max, value = whole_job(M, ms_step, world, pg, dev)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hc, hr, hq = w["centres"], w["radii"], w["charges"]
