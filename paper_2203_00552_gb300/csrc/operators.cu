@@ -11,6 +11,8 @@
 //   The transposes follow the same data in reverse (gathers, no atomics).
 #include <cub/cub.cuh>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 #define BLK 128
@@ -251,6 +253,66 @@ __global__ void k_ab_store(int H, int N, int nb, int L, T kappa, const V4* __res
     for (int l = 0; l <= L; ++l) Rp[(size_t)l * H + h] = ri[tid + l * bd] / rr[tid + l * bd];
     ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
                   [&](int idx, int l, T yv) { Bp[(size_t)idx * H + h] = w * rr[tid + l * bd] * yv; });
+}
+
+// Hit-parallel form of the stored A/B product, step 1: every thread takes hits in a grid
+// stride over all spheres (balanced whatever the per-sphere hit counts) and adds
+// omega u_j(x_i^n) into the global grid arrays gr, ge (zeroed before).
+template <typename T>
+__global__ void __launch_bounds__(256) k_ab_hits_stored(int nb, long long H, const int* __restrict__ hp,
+                                                        const int* __restrict__ hj, const T* __restrict__ Bp,
+                                                        const T* __restrict__ Rp, const T* __restrict__ xr,
+                                                        const T* __restrict__ xe, T* __restrict__ gr,
+                                                        T* __restrict__ ge) {
+    for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += (long long)gridDim.x * blockDim.x) {
+        const int p = hp[h], j = hj[h];
+        const T* Xr = xr + (size_t)j * nb;
+        const T* Xe = xe + (size_t)j * nb;
+        T ur = 0, ue = 0;
+        int l = 0, lend = 1;
+        T rat = Rp[h];
+#pragma unroll 8
+        for (int idx = 0; idx < nb; ++idx) {
+            if (idx == lend) {
+                ++l;
+                lend = (l + 1) * (l + 1);
+                rat = Rp[(size_t)l * H + h];
+            }
+            const T bv = Bp[(size_t)idx * H + h];
+            ur += __ldg(Xr + idx) * bv;
+            ue += __ldg(Xe + idx) * bv * rat;
+        }
+        atomicAdd(gr + p, ur);
+        atomicAdd(ge + p, ue);
+    }
+}
+
+// Step 2: y_i = x_i - sum_n w_n Y_lm(s_n) g_i(n) for both blocks, one CTA per sphere.
+template <typename T, typename V4>
+__global__ void k_ab_project(int M, int N, int nb, const V4* __restrict__ leb, const T* __restrict__ Y,
+                             const T* __restrict__ gr, const T* __restrict__ ge, const T* __restrict__ x,
+                             T* __restrict__ y) {
+    extern __shared__ unsigned char smraw[];
+    T* vr = (T*)smraw;
+    T* ve = vr + N;
+    const int i = blockIdx.x;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        T w = leb[n].w;
+        vr[n] = w * gr[(size_t)i * N + n];
+        ve[n] = w * ge[(size_t)i * N + n];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        T ar = 0, ae = 0;
+        for (int n = 0; n < N; ++n) {
+            T yv = Y[(size_t)n * nb + idx];
+            ar += yv * vr[n];
+            ae += yv * ve[n];
+        }
+        size_t o = (size_t)i * nb + idx;
+        y[o] = x[o] - ar;
+        y[(size_t)M * nb + o] = x[(size_t)M * nb + o] - ae;
+    }
 }
 
 // y = [A x_r ; B x_e] from the stored basis: one CTA per sphere i, one thread per hit,
@@ -747,11 +809,19 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     if (S.stored && !gridR && y && !transpose) {
         using V4 = typename OpSet<T>::V4;
         {
-            size_t smem = sizeof(T) * 2 * (size_t)c->N;
-            KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
-            k_ab_apply_stored<T, V4><<<c->M, 256, smem, c->stream>>>(c->M, c->N, c->nb, L, c->H, S.leb, c->hit_ptr,
-                                                                     S.hps, S.hjs, S.Bp, S.Rp, S.Y, x, y);
-            DDLPB_LAUNCHED(c, "ab_apply_stored");
+            const long long MN = (long long)c->M * c->N;
+            DDLPB_CK(c, cudaMemsetAsync(S.gridA, 0, sizeof(T) * MN, c->stream));
+            DDLPB_CK(c, cudaMemsetAsync(S.gridB, 0, sizeof(T) * MN, c->stream));
+            {
+                KernelTimer kt(c, "ab_apply", sizeof(T) == 4);
+                const int grid = (int)std::min<long long>(ceil_div(c->H, 256), 152LL * 8);
+                k_ab_hits_stored<T><<<grid, 256, 0, c->stream>>>(c->nb, c->H, S.hps, S.hjs, S.Bp, S.Rp, x,
+                                                                 x + (size_t)c->M * c->nb, S.gridA, S.gridB);
+                DDLPB_LAUNCHED(c, "ab_hits_stored");
+            }
+            k_ab_project<T, V4><<<c->M, BLK, sizeof(T) * 2 * (size_t)c->N, c->stream>>>(c->M, c->N, c->nb, S.leb, S.Y,
+                                                                                       S.gridA, S.gridB, x, y);
+            DDLPB_LAUNCHED(c, "ab_project");
             return DDLPB_OK;
         }
     }
