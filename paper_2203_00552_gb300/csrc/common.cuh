@@ -15,6 +15,7 @@
 
 #define DDLPB_LMAX_MAX 16
 #define DDLPB_LT (DDLPB_LMAX_MAX + 4)   // row stride of the (l, m) coefficient tables
+#define DDLPB_TCHUNK 512                // hits per CTA of the transposed A/B product
 
 // ---------------------------------------------------------------------------
 // Tables of the real spherical-harmonic recurrence (Sec. 2.2, Eq. definition_ylm).
@@ -63,6 +64,7 @@ struct OpSet {
     T* extA = nullptr;      // [E] scratch
     T* gridA = nullptr;     // [M*N] scratch
     T* gridB = nullptr;     // [M*N] scratch
+    T* acc = nullptr;       // [2*M*nb] scratch of the transposed A/B product
     // stored basis of the sparse blocks (FP32 set only)
     bool stored = false;
     int nbp = 0;            // nb rounded up to a multiple of 32
@@ -130,6 +132,10 @@ struct ddlpb_ctx {
     int* thit_h = nullptr;      // [H] index of the hit in the point-major list
     double* thit_w = nullptr;   // [H]
     long long H = 0;
+    int* chunk_j = nullptr;     // transposed hit list cut into chunks of at most DDLPB_TCHUNK hits:
+    int* chunk_t0 = nullptr;    // target sphere, first position, count
+    int* chunk_cnt = nullptr;
+    int n_chunks = 0;
     int* ext_ptr = nullptr;     // [M+1] external points grouped by sphere
     int* ext_p = nullptr;       // [E] point index i*N+n
     double4* ext_x = nullptr;   // [E] position and chi

@@ -133,14 +133,16 @@ __global__ void k_ab_apply(int M, int N, int nb, int L, T kappa, const V4* __res
     }
 }
 
-// A^T and B^T: one CTA per sphere j gathers every hit (i, n) -> j.
+// A^T and B^T: the hits (i, n) -> j of every target sphere j, in chunks of at most
+// DDLPB_TCHUNK hits (one CTA each, so that the work is balanced across SMs); each chunk adds
+// its partial sums into acc (zeroed before), and k_ab_transpose_finish forms y = x - acc.
 // zr, ze are the weighted syntheses w_n sum_lm Y_lm(s_n) x_{i lm} of the two blocks.
 template <typename T, typename V4>
 __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
-                               const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ tptr,
+                               const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ chunk_j,
+                               const int* __restrict__ chunk_t0, const int* __restrict__ chunk_cnt,
                                const int* __restrict__ tp, const T* __restrict__ tw, const T* __restrict__ Sinv,
-                               const T* __restrict__ zr, const T* __restrict__ ze, const T* __restrict__ x,
-                               T* __restrict__ y) {
+                               const T* __restrict__ zr, const T* __restrict__ ze, T* __restrict__ acc) {
     extern __shared__ unsigned char smraw[];
     T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
@@ -148,11 +150,11 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
     T* accE = accR + nw * nb;
     T* rr = accE + nw * nb;          // rr | ri | rr (second hit) | ri (second hit), (L+1)*bd each
     T* ri = rr + (L + 1) * bd;
-    const int j = blockIdx.x;
+    const int j = chunk_j[blockIdx.x];
     const V4 b = sph[j];
     for (int k = tid; k < 2 * nw * nb; k += bd) sm[k] = 0;
     __syncthreads();
-    const int t0 = tptr[j], cnt = tptr[j + 1] - t0;
+    const int t0 = chunk_t0[blockIdx.x], cnt = chunk_cnt[blockIdx.x];
     const T* sinv = Sinv + (size_t)j * (L + 2);
     // two hits per thread (base + tid and base + bd + tid), summed before each warp reduction
     for (int base = 0; base < cnt; base += 2 * bd) {
@@ -203,9 +205,16 @@ __global__ void k_ab_transpose(int M, int N, int nb, int L, T kappa, const V4* _
             se += accE[w * nb + idx];
         }
         size_t o = (size_t)j * nb + idx;
-        y[o] = x[o] - sr;
-        y[(size_t)M * nb + o] = x[(size_t)M * nb + o] - se;
+        atomicAdd(acc + o, sr);
+        atomicAdd(acc + (size_t)M * nb + o, se);
     }
+}
+
+template <typename T>
+__global__ void k_ab_transpose_finish(long long n, const T* __restrict__ x, const T* __restrict__ acc,
+                                      T* __restrict__ y) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) y[k] = x[k] - acc[k];
 }
 
 // ---------------------------------------------------------------- A and B, stored basis
@@ -315,78 +324,6 @@ __global__ void k_ab_project(int M, int N, int nb, const V4* __restrict__ leb, c
     }
 }
 
-// y = [A x_r ; B x_e] from the stored basis: one CTA per sphere i, one thread per hit,
-// grid values accumulated per point in shared memory, then projected.  The coefficient
-// loop is flat (the i-ratio changes at l^2) so that the basis loads of several (l, m)
-// are in flight at once.
-template <typename T, typename V4>
-__global__ void __launch_bounds__(256) k_ab_apply_stored(int M, int N, int nb, int L, long long H,
-                                                         const V4* __restrict__ leb, const int* __restrict__ hptr,
-                                                         const int* __restrict__ hp, const int* __restrict__ hj,
-                                                         const T* __restrict__ Bp, const T* __restrict__ Rp,
-                                                         const T* __restrict__ Y, const T* __restrict__ x,
-                                                         T* __restrict__ y) {
-    extern __shared__ unsigned char smraw[];
-    T* vr = (T*)smraw;
-    T* ve = vr + N;
-    const int bd = blockDim.x, tid = threadIdx.x;
-    const int i = blockIdx.x;
-    for (int n = tid; n < N; n += bd) {
-        vr[n] = 0;
-        ve[n] = 0;
-    }
-    __syncthreads();
-    const T* xr = x;
-    const T* xe = x + (size_t)M * nb;
-    const int h0 = hptr[(long long)i * N], h1 = hptr[(long long)(i + 1) * N];
-    // two hits per thread in flight (h and h + bd) for memory-level parallelism
-    for (int ha = h0 + tid; ha < h1; ha += 2 * bd) {
-        const int hb = ha + bd;
-        const bool vb = hb < h1;
-        const int hbb = vb ? hb : ha;
-        const int na = hp[ha] - i * N, ja = hj[ha];
-        const int nbb = hp[hbb] - i * N, jb = hj[hbb];
-        const T* Xra = xr + (size_t)ja * nb;
-        const T* Xea = xe + (size_t)ja * nb;
-        const T* Xrb = xr + (size_t)jb * nb;
-        const T* Xeb = xe + (size_t)jb * nb;
-        T ura = 0, uea = 0, urb = 0, ueb = 0;
-        int l = 0, lend = 1;
-        T rata = Rp[ha], ratb = Rp[hbb];
-#pragma unroll 4
-        for (int idx = 0; idx < nb; ++idx) {
-            if (idx == lend) {
-                ++l;
-                lend = (l + 1) * (l + 1);
-                rata = Rp[(size_t)l * H + ha];
-                ratb = Rp[(size_t)l * H + hbb];
-            }
-            const T ba = Bp[(size_t)idx * H + ha], bb = Bp[(size_t)idx * H + hbb];
-            ura += __ldg(Xra + idx) * ba;
-            uea += __ldg(Xea + idx) * ba * rata;
-            urb += __ldg(Xrb + idx) * bb;
-            ueb += __ldg(Xeb + idx) * bb * ratb;
-        }
-        atomicAdd(vr + na, ura);
-        atomicAdd(ve + na, uea);
-        if (vb) {
-            atomicAdd(vr + nbb, urb);
-            atomicAdd(ve + nbb, ueb);
-        }
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nb; idx += bd) {
-        T ar = 0, ae = 0;
-        for (int n = 0; n < N; ++n) {
-            T wy = leb[n].w * Y[(size_t)n * nb + idx];
-            ar += wy * vr[n];
-            ae += wy * ve[n];
-        }
-        size_t o = (size_t)i * nb + idx;
-        y[o] = xr[o] - ar;
-        y[(size_t)M * nb + o] = xe[o] - ae;
-    }
-}
 
 // ---------------------------------------------------------------- dense coupling (L_C)
 
@@ -711,6 +648,7 @@ ddlpb_status opset_prepare<double>(ddlpb_ctx* c, OpSet<double>& S) {
     S.extA = c->extA;
     S.gridA = c->gridA;
     S.gridB = c->gridB;
+    DDLPB_TRY(ctx_alloc(c, &S.acc, 2 * (size_t)c->M * c->nb));
     S.ready = true;
     return DDLPB_OK;
 }
@@ -751,6 +689,7 @@ ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
     DDLPB_TRY(ctx_alloc(c, &S.extA, c->E));
     DDLPB_TRY(ctx_alloc(c, &S.gridA, MN));
     DDLPB_TRY(ctx_alloc(c, &S.gridB, MN));
+    DDLPB_TRY(ctx_alloc(c, &S.acc, 2 * (size_t)M * nb));
     DDLPB_CK(c, cudaMemsetAsync(S.mu, 0, sizeof(float) * M * nb, c->stream));
     // stored basis of the sparse blocks (FP32, two layouts)
     const long long H = c->H;
@@ -838,11 +777,18 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     DDLPB_TRY(synthesis_T<T>(c, S, x + (size_t)c->M * c->nb, c->M, S.gridB, true));
     size_t smem = sizeof(T) * (2 * (size_t)(BLK / 32) * c->nb + 4 * (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_ab_transpose<T, typename OpSet<T>::V4>, smem));
-    KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
-    k_ab_transpose<T><<<c->M, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
-                                                      c->thit_ptr, c->thit_p, S.thit_w, S.Sinv, S.gridA, S.gridB, x,
-                                                      y);
-    DDLPB_LAUNCHED(c, "ab_transpose");
+    const long long nv = 2LL * c->M * c->nb;
+    DDLPB_CK(c, cudaMemsetAsync(S.acc, 0, sizeof(T) * nv, c->stream));
+    if (c->n_chunks > 0) {
+        KernelTimer kt(c, "ab_transpose", sizeof(T) == 4);
+        k_ab_transpose<T><<<c->n_chunks, BLK, smem, c->stream>>>(c->M, c->N, c->nb, L, (T)c->kappa, S.sph, S.leb,
+                                                                 S.yt, c->chunk_j, c->chunk_t0, c->chunk_cnt,
+                                                                 c->thit_p, S.thit_w, S.Sinv, S.gridA, S.gridB,
+                                                                 S.acc);
+        DDLPB_LAUNCHED(c, "ab_transpose");
+    }
+    k_ab_transpose_finish<T><<<ceil_div(nv, 256), 256, 0, c->stream>>>(nv, x, S.acc, y);
+    DDLPB_LAUNCHED(c, "ab_transpose_finish");
     return DDLPB_OK;
 }
 

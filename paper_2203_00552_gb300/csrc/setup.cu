@@ -248,6 +248,23 @@ __global__ void k_rhs_combine(long long half, const double* __restrict__ G0, con
     }
 }
 
+__global__ void k_chunk_count(int M, const int* __restrict__ tptr, int* __restrict__ cnt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < M) cnt[j] = (tptr[j + 1] - tptr[j] + DDLPB_TCHUNK - 1) / DDLPB_TCHUNK;
+}
+
+__global__ void k_chunk_fill(int M, const int* __restrict__ tptr, const int* __restrict__ cpos,
+                             int* __restrict__ cj, int* __restrict__ ct0, int* __restrict__ ccnt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int o = cpos[j];
+    for (int t = tptr[j]; t < tptr[j + 1]; t += DDLPB_TCHUNK, ++o) {
+        cj[o] = j;
+        ct0[o] = t;
+        ccnt[o] = min(DDLPB_TCHUNK, tptr[j + 1] - t);
+    }
+}
+
 // ---------------------------------------------------------------- host helpers
 
 static ddlpb_status scan_exclusive(ddlpb_ctx* c, const int* in, int* out, long long n) {
@@ -433,6 +450,25 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
         }
         k_segment_starts<<<ceil_div(H + 1, 256), 256, 0, st>>>(H, M, keys_out, c->thit_ptr);
         DDLPB_LAUNCHED(c, "segment_starts");
+    }
+
+    // -- chunks of the transposed hit list (work units of the transposed A/B product)
+    {
+        int *ccnt = nullptr, *cpos = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &ccnt, M + 1));
+        DDLPB_TRY(ctx_alloc(c, &cpos, M + 1));
+        DDLPB_CK(c, cudaMemsetAsync(ccnt, 0, sizeof(int) * (M + 1), st));
+        k_chunk_count<<<ceil_div(M, 256), 256, 0, st>>>(M, c->thit_ptr, ccnt);
+        DDLPB_LAUNCHED(c, "chunk_count");
+        DDLPB_TRY(scan_exclusive(c, ccnt, cpos, M + 1));
+        int nch = 0;
+        DDLPB_TRY(read_int(c, cpos + M, &nch));
+        c->n_chunks = nch;
+        DDLPB_TRY(ctx_alloc(c, &c->chunk_j, nch));
+        DDLPB_TRY(ctx_alloc(c, &c->chunk_t0, nch));
+        DDLPB_TRY(ctx_alloc(c, &c->chunk_cnt, nch));
+        k_chunk_fill<<<ceil_div(M, 256), 256, 0, st>>>(M, c->thit_ptr, cpos, c->chunk_j, c->chunk_t0, c->chunk_cnt);
+        DDLPB_LAUNCHED(c, "chunk_fill");
     }
 
     // -- external points (chi_i^eta > 0) and the spheres that own them
