@@ -381,8 +381,11 @@ __global__ void k_yukawa_pot(int E, const V4* __restrict__ ext_x, int n_src, con
     if (valid) xt = ext_x[t];
     else xt.x = xt.y = xt.z = xt.w = 0;
     T acc = 0;
-    for (int base = 0; base < n_src; base += YK_TS) {
-        int ns = min(YK_TS, n_src - base);
+    // sources of this CTA: group blockIdx.y of gridDim.y (partials added atomically when split)
+    const int per = ((n_src + gridDim.y - 1) / gridDim.y + YK_TS - 1) / YK_TS * YK_TS;
+    const int s_begin = blockIdx.y * per, s_end = min(n_src, s_begin + per);
+    for (int base = s_begin; base < s_end; base += YK_TS) {
+        int ns = min(YK_TS, s_end - base);
         __syncthreads();
         for (int k = tid; k < ns * nb; k += bd) {
             int s = k / nb, idx = k % nb;
@@ -406,7 +409,10 @@ __global__ void k_yukawa_pot(int E, const V4* __restrict__ ext_x, int n_src, con
             acc += v;
         }
     }
-    if (valid) phi[t] = acc;
+    if (valid) {
+        if (gridDim.y > 1) atomicAdd(phi + t, acc);
+        else phi[t] = acc;
+    }
 }
 
 // nu_j = sum_t c_t k_l^j(x_t) Y_lm^j(x_t) (transpose of k_yukawa_pot), one CTA per source j.
@@ -424,10 +430,13 @@ __global__ void k_yukawa_adj(int E, const V4* __restrict__ ext_x, const T* __res
     for (int k = tid; k < nw * nb; k += bd) acc[k] = 0;
     for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
     __syncthreads();
-    for (int base = 0; base < E; base += bd) {
+    // targets of this CTA: chunk blockIdx.y of gridDim.y (partials added atomically when split)
+    const int per = ((E + gridDim.y - 1) / gridDim.y + bd - 1) / bd * bd;
+    const int t_begin = blockIdx.y * per, t_end = min(E, t_begin + per);
+    for (int base = t_begin; base < t_end; base += bd) {
         int t = base + tid;
         T dx = b.w, dy = 0, dz = 0, c = 0;
-        if (t < E) {
+        if (t < t_end) {
             V4 xt = ext_x[t];
             dx = xt.x - b.x;
             dy = xt.y - b.y;
@@ -526,7 +535,8 @@ __global__ void k_yukawa_local_adj(int nb, int L, T kappa, const int* __restrict
     for (int idx = tid; idx < nb; idx += bd) {
         T s = 0;
         for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
-        nu[(size_t)j * nb + idx] = s;
+        if (gridDim.y > 1) atomicAdd(nu + (size_t)j * nb + idx, s);
+        else nu[(size_t)j * nb + idx] = s;
     }
 }
 
@@ -811,9 +821,13 @@ static ddlpb_status yukawa_pot_T(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_
     size_t smem = sizeof(V4) * YK_TS + sizeof(T) * (YK_TS * (size_t)c->nb + YK_TS * (size_t)(L + 2) +
                                                      (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_yukawa_pot<T, V4>, smem));
+    // at least ~4 CTAs per SM: split the sources when the targets alone give too few CTAs
+    const int cx = ceil_div(c->E, BLK);
+    const int sy = std::max(1, std::min(ceil_div(608, cx), ceil_div(c->n_src, 4 * YK_TS)));
+    if (sy > 1) DDLPB_CK(c, cudaMemsetAsync(phi_ext, 0, sizeof(T) * c->E, c->stream));
     KernelTimer kt(c, "yukawa_pot", sizeof(T) == 4);
-    k_yukawa_pot<T><<<ceil_div(c->E, BLK), BLK, smem, c->stream>>>(c->E, S.ext_x, c->n_src, c->src, S.sph, mu,
-                                                                   S.Khinv, c->nb, L, (T)c->kappa, S.yt, phi_ext);
+    k_yukawa_pot<T><<<dim3(cx, sy), BLK, smem, c->stream>>>(c->E, S.ext_x, c->n_src, c->src, S.sph, mu, S.Khinv,
+                                                            c->nb, L, (T)c->kappa, S.yt, phi_ext);
     DDLPB_LAUNCHED(c, "yukawa_pot");
     return DDLPB_OK;
 }
@@ -825,9 +839,12 @@ static ddlpb_status yukawa_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* n
     using V4 = typename OpSet<T>::V4;
     size_t smem = sizeof(T) * ((size_t)(BLK / 32) * c->nb + (L + 2) + (size_t)(L + 1) * BLK);
     DDLPB_TRY(set_smem(c, (const void*)k_yukawa_adj<T, V4>, smem));
+    // at least ~4 CTAs per SM: split the targets when the sources alone give too few CTAs
+    const int ty = std::max(1, std::min(ceil_div(608, c->n_src), ceil_div(c->E, 4 * BLK)));
+    if (ty > 1) DDLPB_CK(c, cudaMemsetAsync(nu, 0, sizeof(T) * (size_t)c->M * c->nb, c->stream));
     KernelTimer kt(c, "yukawa_adj", sizeof(T) == 4);
-    k_yukawa_adj<T><<<c->n_src, BLK, smem, c->stream>>>(c->E, S.ext_x, c_ext, c->src, S.sph, S.Khinv, c->nb, L,
-                                                        (T)c->kappa, S.yt, nu);
+    k_yukawa_adj<T><<<dim3(c->n_src, ty), BLK, smem, c->stream>>>(c->E, S.ext_x, c_ext, c->src, S.sph, S.Khinv,
+                                                                  c->nb, L, (T)c->kappa, S.yt, nu);
     DDLPB_LAUNCHED(c, "yukawa_adj");
     return DDLPB_OK;
 }
