@@ -454,7 +454,8 @@ __global__ void k_yukawa_adj(int E, const V4* __restrict__ ext_x, const T* __res
     for (int idx = tid; idx < nb; idx += bd) {
         T s = 0;
         for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
-        nu[(size_t)j * nb + idx] = s;
+        if (gridDim.y > 1) atomicAdd(nu + (size_t)j * nb + idx, s);
+        else nu[(size_t)j * nb + idx] = s;
     }
 }
 
@@ -535,8 +536,7 @@ __global__ void k_yukawa_local_adj(int nb, int L, T kappa, const int* __restrict
     for (int idx = tid; idx < nb; idx += bd) {
         T s = 0;
         for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
-        if (gridDim.y > 1) atomicAdd(nu + (size_t)j * nb + idx, s);
-        else nu[(size_t)j * nb + idx] = s;
+        nu[(size_t)j * nb + idx] = s;
     }
 }
 
