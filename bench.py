@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64 comparison")
     ap.add_argument("--ops-only", action="store_true",
                     help="setup plus one application of each FP32 operator, then exit (for ncu captures)")
     return ap.parse_args()
@@ -220,9 +221,10 @@ def main():
         ctx.close()
         return
 
-    def step(timing=False):
+    def step(timing=False, options=None):
         ctx = G.Context(cen, rad, chg, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"],
-                        surface=w["surface"], stream=stream.cuda_stream, kernel_timing=1 if timing else 0, **opts)
+                        surface=w["surface"], stream=stream.cuda_stream, kernel_timing=1 if timing else 0,
+                        **(options or opts))
         ctx.solve()
         ctx.adjoint()
         ctx.energy_device(e_out)
@@ -283,6 +285,26 @@ def main():
                "h2d_bytes_per_step": int(hc.nbytes + hr.nbytes + hq.nbytes),
                "d2h_bytes_per_step": int(F.nbytes + 8)}
 
+    # the plain FP64 path on the same workload, one step, for comparison with the mixed form
+    fp64 = None
+    if prec == G.DDLPB_MIXED and not args.no_fp64 and rank == 0:
+        e_mixed = float(e_out.item())
+        f_mixed = f_out.clone()
+        o64 = dict(opts, precision=G.DDLPB_FP64)
+        step(options=o64).close()   # warm-up of the FP64 kernels
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step(options=o64).close()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        e64 = float(e_out.item())
+        fp64 = {"ms_per_step": ms64, "value": M / (ms64 / 1e3), "unit": UNIT, "speedup_of_mixed": ms64 / t_max,
+                "energy_rel_diff_mixed_vs_fp64": abs(e_mixed - e64) / abs(e64),
+                "force_rel_diff_mixed_vs_fp64": float((f_mixed - f_out).norm() / f_out.norm())}
+
     # roofline of the dominant instrumented kernel
     info = infos[-1]
     nb = (w["lmax"] + 1) ** 2
@@ -330,7 +352,7 @@ def main():
                            "tol": 1e-8, "gmres_restart": args.restart, "precond_tol": args.precond_tol,
                            "l2": "512 MB buffer written between timed steps; working set > L2",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "fp64_path": fp64,
                 "cpu_baseline": cpu, "clocks": clocks,
                 "solver": {"outer": info["solve_iterations"], "adjoint_outer": info["adjoint_iterations"],
                            "refinement": info["refinement_steps"], "residual": info["solve_residual"],

@@ -65,8 +65,8 @@ struct OpSet {
     T* gridA = nullptr;     // [M*N] scratch
     T* gridB = nullptr;     // [M*N] scratch
     T* acc = nullptr;       // [2*M*nb] scratch of the transposed A/B product
-    // stored basis of the sparse blocks (FP32 set only)
-    bool stored = false;
+    // stored basis of the forward A/B product (built on its first use)
+    bool stored = false, store_tried = false;
     int nbp = 0;            // nb rounded up to a multiple of 32
     T* Bp = nullptr;        // [nb][H]   omega r^l Y; within a sphere, hits ordered by (neighbour, point)
     T* Rp = nullptr;        // [L+1][H]  i-ratio corrections, same order

@@ -701,35 +701,41 @@ ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
     DDLPB_TRY(ctx_alloc(c, &S.gridB, MN));
     DDLPB_TRY(ctx_alloc(c, &S.acc, 2 * (size_t)M * nb));
     DDLPB_CK(c, cudaMemsetAsync(S.mu, 0, sizeof(float) * M * nb, c->stream));
-    // stored basis of the sparse blocks (FP32, two layouts)
-    const long long H = c->H;
-    S.nbp = ((nb + 31) / 32) * 32;
-    if (H > 0) {
-        unsigned long long *kin = nullptr, *kout = nullptr;
-        int *vin = nullptr, *order = nullptr;
-        DDLPB_TRY(ctx_alloc(c, &kin, H));
-        DDLPB_TRY(ctx_alloc(c, &kout, H));
-        DDLPB_TRY(ctx_alloc(c, &vin, H));
-        DDLPB_TRY(ctx_alloc(c, &order, H));
-        k_store_keys<<<ceil_div(H, 256), 256, 0, c->stream>>>((int)H, N, c->hit_p, c->hit_s, kin, vin);
-        DDLPB_LAUNCHED(c, "store_keys");
-        size_t bytes = 0;
-        DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(nullptr, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
-        void* tmp = nullptr;
-        DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
-        DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(tmp, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
-        DDLPB_TRY(ctx_alloc(c, &S.Bp, (size_t)nb * H));
-        DDLPB_TRY(ctx_alloc(c, &S.Rp, (size_t)(L + 1) * H));
-        DDLPB_TRY(ctx_alloc(c, &S.hps, H));
-        DDLPB_TRY(ctx_alloc(c, &S.hjs, H));
-        size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
-        k_ab_store<float><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, L, (float)c->kappa, S.sph, S.leb,
-                                                                      S.yt, order, c->hit_p, c->hit_j, S.hit_w, S.Sinv,
-                                                                      S.Bp, S.Rp, S.hps, S.hjs);
-        DDLPB_LAUNCHED(c, "ab_store");
-        S.stored = true;
-    }
     S.ready = true;
+    return DDLPB_OK;
+}
+
+// Stored basis of the forward A/B product (built on the first forward application).
+template <typename T>
+static ddlpb_status build_stored(ddlpb_ctx* c, OpSet<T>& S) {
+    S.store_tried = true;
+    const int N = c->N, nb = c->nb, L = c->lmax;
+    const long long H = c->H;
+    if (H <= 0) return DDLPB_OK;
+    unsigned long long *kin = nullptr, *kout = nullptr;
+    int *vin = nullptr, *order = nullptr;
+    DDLPB_TRY(ctx_alloc(c, &kin, H));
+    DDLPB_TRY(ctx_alloc(c, &kout, H));
+    DDLPB_TRY(ctx_alloc(c, &vin, H));
+    DDLPB_TRY(ctx_alloc(c, &order, H));
+    k_store_keys<<<ceil_div(H, 256), 256, 0, c->stream>>>((int)H, N, c->hit_p, c->hit_s, kin, vin);
+    DDLPB_LAUNCHED(c, "store_keys");
+    size_t bytes = 0;
+    DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(nullptr, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
+    void* tmp = nullptr;
+    DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+    DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(tmp, bytes, kin, kout, vin, order, (int)H, 0, 64, c->stream));
+    DDLPB_TRY(ctx_alloc(c, &S.Bp, (size_t)nb * H));
+    DDLPB_TRY(ctx_alloc(c, &S.Rp, (size_t)(L + 1) * H));
+    DDLPB_TRY(ctx_alloc(c, &S.hps, H));
+    DDLPB_TRY(ctx_alloc(c, &S.hjs, H));
+    size_t smem = sizeof(T) * 2 * (size_t)(L + 1) * BLK;
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<T, typename OpSet<T>::V4>, smem));
+    k_ab_store<T><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
+                                                             order, c->hit_p, c->hit_j, S.hit_w, S.Sinv, S.Bp, S.Rp,
+                                                             S.hps, S.hjs);
+    DDLPB_LAUNCHED(c, "ab_store");
+    S.stored = true;
     return DDLPB_OK;
 }
 
@@ -755,6 +761,7 @@ template <typename T>
 ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE) {
     DDLPB_TRY(opset_prepare<T>(c, S));
     const int L = c->lmax;
+    if (!transpose && y && !gridR && !S.store_tried) DDLPB_TRY(build_stored<T>(c, S));
     if (S.stored && !gridR && y && !transpose) {
         using V4 = typename OpSet<T>::V4;
         {

@@ -165,8 +165,9 @@ def test_device_setup_and_outputs_match_host():
     d.energy_device(e)
     f = torch.empty((12, 3), dtype=torch.float64, device=DEV)
     d.forces_device(f)
-    assert float(e) == h.energy()
-    assert np.array_equal(f.cpu().numpy(), h.forces())
+    # same inputs, same result up to the order of the atomic accumulations
+    assert abs(float(e) - h.energy()) <= 1e-13 * abs(h.energy())
+    assert np.abs(f.cpu().numpy() - h.forces()).max() <= 1e-12 * np.abs(h.forces()).max()
 
 
 def test_error_paths():
