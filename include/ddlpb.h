@@ -23,7 +23,9 @@
  * context owns all device memory it allocates and frees it in ddlpb_free.
  * Every call runs on the CUDA stream given in ddlpb_options.cuda_stream (NULL:
  * the legacy default stream) and returns only after its results are
- * available to the caller.
+ * available to the caller.  Device memory is allocated and freed stream-ordered
+ * on that stream, so contexts on different streams (driven from different host
+ * threads) run concurrently.
  *
  * Errors: every call returns a ddlpb_status and never aborts the process.  On
  * error, ddlpb_last_error(ctx) returns a message (for a failed setup the
@@ -178,6 +180,14 @@ DDLPB_API ddlpb_status ddlpb_kernel_time(ddlpb_ctx* ctx, const char* name, long 
 
 /* Reset the kernel timers. */
 DDLPB_API ddlpb_status ddlpb_kernel_time_reset(ddlpb_ctx* ctx);
+
+/* Initial guess for the next solve: which = 1 sets X (for ddlpb_solve), which = 2 sets
+ * X_adj (for ddlpb_adjoint); x is device memory in the layout above.  Used to warm-start a
+ * geometry close to an earlier one with that one's solutions (the reuse of the previous
+ * iterate that Sec. 4 makes inside its solver, carried across geometries).  Resets the
+ * call-order state: ddlpb_solve (and ddlpb_adjoint) must run again.  DDLPB_EINVAL for
+ * another which. */
+DDLPB_API ddlpb_status ddlpb_set_vector_device(ddlpb_ctx* ctx, int which, const double* x);
 
 /* Counters and solver statistics. */
 DDLPB_API ddlpb_status ddlpb_get_info(const ddlpb_ctx* ctx, ddlpb_info* info);

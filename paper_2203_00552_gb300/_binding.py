@@ -49,7 +49,8 @@ _lib = None
 EXPORTS = ["ddlpb_default_options", "ddlpb_setup", "ddlpb_setup_device", "ddlpb_solve", "ddlpb_adjoint",
            "ddlpb_energy", "ddlpb_energy_device", "ddlpb_forces", "ddlpb_forces_device", "ddlpb_apply_device",
            "ddlpb_get_vector_device", "ddlpb_get_info", "ddlpb_last_error", "ddlpb_last_setup_error", "ddlpb_free",
-           "ddlpb_kernel_time", "ddlpb_kernel_time_reset", "ddlpb_energy_noalloc", "ddlpb_noalloc_last_error"]
+           "ddlpb_kernel_time", "ddlpb_kernel_time_reset", "ddlpb_energy_noalloc", "ddlpb_noalloc_last_error",
+           "ddlpb_set_vector_device"]
 
 
 def library():
@@ -80,6 +81,8 @@ def library():
     lib.ddlpb_apply_device.restype = C.c_int
     lib.ddlpb_get_vector_device.argtypes = [P, C.c_int, P]
     lib.ddlpb_get_vector_device.restype = C.c_int
+    lib.ddlpb_set_vector_device.argtypes = [P, C.c_int, P]
+    lib.ddlpb_set_vector_device.restype = C.c_int
     lib.ddlpb_get_info.argtypes = [P, C.POINTER(Info)]
     lib.ddlpb_get_info.restype = C.c_int
     lib.ddlpb_last_error.argtypes = [P]
@@ -196,6 +199,10 @@ class Context:
         """Copy g (0), X (1) or X_adj (2) into the device tensor out."""
         self._check(library().ddlpb_get_vector_device(self._h, int(which), _ptr(out)))
         return out
+
+    def set_vector(self, which: int, x):
+        """Initial guess for the next solve: X (1) or X_adj (2), from the device tensor x."""
+        self._check(library().ddlpb_set_vector_device(self._h, int(which), _ptr(x)))
 
     def info(self) -> dict:
         i = Info()

@@ -156,7 +156,7 @@ struct ddlpb_ctx {
 
     // scratch
     void* solver = nullptr;     // Krylov workspaces (solve.cu)
-    std::vector<void*> pinned;  // pinned host buffers
+    std::vector<double*> host_bufs;  // host mirrors of the Krylov scalars
     double* mu = nullptr;       // [M][nb]
     double* gridA = nullptr;    // [M*N]
     double* gridB = nullptr;    // [M*N]
@@ -203,10 +203,11 @@ template <typename T>
 static ddlpb_status ctx_alloc(ddlpb_ctx* c, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    // stream-ordered: no device-wide synchronisation, so contexts on other streams keep running
+    cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        c->err = std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes: " +
+        c->err = std::string("cudaMallocAsync of ") + std::to_string(count * sizeof(T)) + " bytes: " +
                  cudaGetErrorString(e);
         return e == cudaErrorMemoryAllocation ? DDLPB_ENOMEM : DDLPB_ECUDA;
     }

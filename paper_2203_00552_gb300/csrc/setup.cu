@@ -308,9 +308,10 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
     // -- inputs to host for validation
     std::vector<double> hc(3 * (size_t)M), hr(M), hq(M);
     if (device_ptrs) {
-        DDLPB_CK(c, cudaMemcpy(hc.data(), centres, 3 * sizeof(double) * M, cudaMemcpyDeviceToHost));
-        DDLPB_CK(c, cudaMemcpy(hr.data(), radii, sizeof(double) * M, cudaMemcpyDeviceToHost));
-        DDLPB_CK(c, cudaMemcpy(hq.data(), charges, sizeof(double) * M, cudaMemcpyDeviceToHost));
+        DDLPB_CK(c, cudaMemcpyAsync(hc.data(), centres, 3 * sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+        DDLPB_CK(c, cudaMemcpyAsync(hr.data(), radii, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+        DDLPB_CK(c, cudaMemcpyAsync(hq.data(), charges, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream));
+        DDLPB_CK(c, cudaStreamSynchronize(c->stream));
     } else {
         std::memcpy(hc.data(), centres, 3 * sizeof(double) * M);
         std::memcpy(hr.data(), radii, sizeof(double) * M);

@@ -160,7 +160,7 @@ struct Krylov {
     T* r = nullptr;
     double* red = nullptr;
     double* h = nullptr;   // h1 | h2 | nrm | scalar slots
-    double* hp = nullptr;  // pinned host mirror
+    double* hp = nullptr;  // host mirror
 };
 
 template <typename T>
@@ -173,8 +173,9 @@ static ddlpb_status krylov_alloc(ddlpb_ctx* c, Krylov<T>& K, int m, long long n,
     DDLPB_TRY(ctx_alloc(c, &K.r, n));
     DDLPB_TRY(ctx_alloc(c, &K.red, (size_t)RGRID * (m + 2)));
     DDLPB_TRY(ctx_alloc(c, &K.h, 4 * (size_t)(m + 2)));
-    DDLPB_CK(c, cudaMallocHost((void**)&K.hp, sizeof(double) * 4 * (m + 2)));
-    c->pinned.push_back(K.hp);
+    // pageable host mirror: every copy into it is followed by a stream synchronisation anyway
+    K.hp = new double[4 * (size_t)(m + 2)];
+    c->host_bufs.push_back(K.hp);
     return DDLPB_OK;
 }
 
@@ -719,6 +720,22 @@ extern "C" ddlpb_status ddlpb_kernel_time_reset(ddlpb_ctx* c) {
     return DDLPB_OK;
 }
 
+extern "C" ddlpb_status ddlpb_set_vector_device(ddlpb_ctx* c, int which, const double* x) {
+    if (!c || !x || (which != 1 && which != 2)) return DDLPB_EINVAL;
+    c->err.clear();
+    double* d = which == 1 ? c->X : c->Xa;
+    DDLPB_CK(c, cudaMemcpyAsync(d, x, sizeof(double) * c->nvec, cudaMemcpyDeviceToDevice, c->stream));
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    if (which == 1) {
+        c->X_zero = false;
+        c->solved = false;
+    } else {
+        c->Xa_zero = false;
+    }
+    c->adjoint_done = false;
+    return DDLPB_OK;
+}
+
 extern "C" ddlpb_status ddlpb_get_info(const ddlpb_ctx* c, ddlpb_info* info) {
     if (!c || !info) return DDLPB_EINVAL;
     *info = c->info;
@@ -733,8 +750,9 @@ extern "C" void ddlpb_free(ddlpb_ctx* c) {
     if (!c) return;
     for (auto& kv : c->ktimes)
         for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
-    for (void* p : c->allocs) cudaFree(p);
-    for (void* p : c->pinned) cudaFreeHost(p);
+    for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
+    cudaStreamSynchronize(c->stream);
+    for (double* p : c->host_bufs) delete[] p;
     solver_state_free(c);
     delete c;
 }

@@ -1,0 +1,106 @@
+"""Serving driver: request stream, admission and slot accounting (CPU, fake engine), and on
+the GPU that every request's result is the same alone and in the concurrent mix."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2203_00552_gb300 import serve
+
+
+def test_request_stream_is_seeded_and_poisson():
+    a = serve.make_requests(3, rate=50.0, duration=4.0, size_min=5, size_max=40)
+    b = serve.make_requests(3, rate=50.0, duration=4.0, size_min=5, size_max=40)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    assert all(np.array_equal(x.centres, y.centres) for x, y in zip(a, b))
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    # exponential gaps: mean 1/rate, coefficient of variation near 1
+    assert abs(gaps.mean() - 1 / 50.0) < 0.3 / 50.0
+    assert 0.7 < gaps.std() / gaps.mean() < 1.3
+    assert all(5 <= r.atoms <= 40 for r in a)
+    pert = [r for r in a if r.parent is not None]
+    assert 0.15 < len(pert) / len(a) < 0.45
+    for r in pert:
+        p = a[r.parent]
+        assert p.arrival < r.arrival and p.lmax == r.lmax and r.atoms == p.atoms
+        d = np.abs(r.centres - p.centres).max()
+        assert 0 < d < 0.02 * serve.synth.ANGSTROM_TO_BOHR * 6
+    assert {r.n_lebedev for r in a} <= {serve.GRIDS[6], serve.GRIDS[8]}
+
+
+def test_footprint_grows_with_size_and_degree():
+    f = serve.footprint_bytes
+    assert f(200, 6, 110, 300) < f(400, 6, 110, 300) < f(400, 8, 302, 300)
+    assert f(1000, 8, 302, 300) < 8 * 2 ** 30
+
+
+class _Fake:
+    """Engine that sleeps in proportion to the size and records concurrency."""
+
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.active = 0
+        self.max_active = 0
+        self.warm = []
+
+    def __call__(self, req, warm):
+        with self.lock:
+            self.active += 1
+            self.max_active = max(self.max_active, self.active)
+            self.warm.append((req.rid, warm))
+        time.sleep(0.002 + 1e-4 * req.atoms)
+        with self.lock:
+            self.active -= 1
+        if req.rid == 5:
+            raise RuntimeError("planted failure")
+        return float(req.atoms), np.zeros((req.atoms, 3)), ("X", req.rid), 1
+
+
+def test_server_respects_slots_budget_and_arrivals():
+    reqs = serve.make_requests(1, rate=400.0, duration=0.15, size_min=5, size_max=60)
+    eng = _Fake()
+    srv = serve.Server(eng, slots=3, hbm_budget=10 ** 15)
+    res, makespan = srv.run(reqs)
+    assert [r.rid for r in res] == [r.rid for r in reqs]
+    assert eng.max_active <= 3 and srv.peak_inflight <= 3
+    for q, r in zip(reqs, res):
+        assert r.start >= q.arrival - 1e-6
+        assert r.latency >= r.end - r.start
+    assert "error" in res[5].extra and sum("error" in r.extra for r in res) == 1
+    s = serve.summary(res, makespan)
+    assert s["requests"] == len(reqs) and s["errors"] == 1 and s["p99_ms"] >= s["p50_ms"]
+    # a perturbed request whose parent finished before it started gets the parent's solution
+    done = {r.rid: r for r in res}
+    for rid, warm in eng.warm:
+        q = reqs[rid]
+        if q.parent is not None and q.parent != 5 and done[q.parent].end < done[rid].start - 1e-3:
+            assert warm == ("X", q.parent)
+
+
+def test_server_admits_one_oversized_request_alone():
+    reqs = serve.make_requests(2, rate=300.0, duration=0.1, size_min=10, size_max=30)
+    eng = _Fake()
+    tiny = min(serve.footprint_bytes(r.atoms, r.lmax, r.n_lebedev, 300) for r in reqs)
+    srv = serve.Server(eng, slots=8, hbm_budget=tiny - 1)
+    res, _ = srv.run(reqs)
+    # nothing fits the budget, so each runs alone
+    assert eng.max_active == 1 and len(res) == len(reqs)
+
+
+@pytest.mark.gpu
+def test_served_results_match_solo_runs():
+    """Each request gives the same energy and forces in the concurrent mix (4 slots, shared
+    GPU, warm starts) as alone on a fresh context from a zero start: 1e-6 relative energy,
+    1e-5 relative force norm (both within the mixed form's 1e-8 solver tolerance)."""
+    torch = pytest.importorskip("torch")
+    reqs = serve.make_requests(4, rate=40.0, duration=0.4, size_min=20, size_max=120)
+    eng = serve.gpu_engine()
+    res, _ = serve.Server(eng, slots=4, hbm_budget=64 * 2 ** 30).run(reqs)
+    assert all("error" not in r.extra for r in res)
+    assert sum(r.warm for r in res) >= 1
+    for q, r in zip(reqs, res):
+        e, f, _, _ = eng(q, None)
+        assert abs(r.energy - e) <= 1e-6 * abs(e)
+        assert np.linalg.norm(r.forces - f) <= 1e-5 * np.linalg.norm(f)
+    torch.cuda.synchronize()
