@@ -40,8 +40,11 @@ FP32_PEAK_TFLOPS_AT_MAX_CLOCK = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 la
 FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8}
 HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
 # dram bytes per launch from the committed ncu capture (profiles/), keyed by (kernel, workload),
-# with the digest of the operator sources they were taken on; null once those sources change.
-NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2154332160, "digest": "4cce5c8c6b9c5769"}}
+# with the digest of the kernel's source text they were taken on; null once that text changes.
+NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2153989632, "digest": "95c4403a9005b218"}}
+# CUDA functions whose source text a timed kernel name stands for
+KERNEL_SOURCES = {"ab_apply_f32": ["k_ab_hits_stored"], "ab_apply_f16": ["half8_to_float", "k_ab_hits_half"],
+                  "ab_transpose_f16": ["half8_to_float", "k_ab_transpose_half"]}
 
 
 def parse():
@@ -158,13 +161,25 @@ def whole_job(atoms_per_rank, ms_local, world, dist=None, device="cpu"):
     return t_max, world * atoms_per_rank / (t_max / 1e3)
 
 
-def source_digest():
+def kernel_digest(kernel):
+    """Digest of the source text (definition through its closing brace) of the CUDA functions
+    behind a timed kernel name; None if a function is not found."""
     import hashlib
+    with open(os.path.join(ROOT, "paper_2203_00552_gb300", "csrc", "operators.cu")) as f:
+        text = f.read()
     h = hashlib.sha256()
-    for name in ("operators.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2203_00552_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    for fn in KERNEL_SOURCES.get(kernel, []):
+        i = text.find(" " + fn + "(")
+        if i < 0:
+            return None
+        j = text.index("{", i)
+        depth = 0
+        for k in range(j, len(text)):
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            if depth == 0:
+                break
+        h.update(text[i:k + 1].encode())
+    return h.hexdigest()[:16] if kernel in KERNEL_SOURCES else None
 
 
 def main():
@@ -313,15 +328,18 @@ def main():
              "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
     roofline = None
     L = w["lmax"]
-    # The FP32 A/B product streams a stored basis (HBM-bound): algorithmic bytes per hit are
-    # the basis row (nb + lmax + 1 floats) plus the hit's point and sphere indices (8 B).
-    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8)}
+    # The stored A/B products stream the basis (HBM-bound): algorithmic bytes per hit are the
+    # basis row (nb + lmax + 1 values) plus the hit's indices (point and sphere: 8 B in the FP32
+    # layout; the point alone in the FP16 layout, whose sphere is per group of 8 hits).
+    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8),
+                    "ab_apply_f16": info["n_hits"] * ((nb + L + 1) * 2 + 4),
+                    "ab_transpose_f16": info["n_hits"] * ((nb + L + 1) * 2 + 4)}
     if kstats:
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]
         base = top.rsplit("_", 1)[0]
         tr = NCU_TRAFFIC.get((top, args.workload))
-        traffic = tr["bytes_per_launch"] if tr and tr.get("digest") == source_digest() else None
+        traffic = tr["bytes_per_launch"] if tr and tr.get("digest") == kernel_digest(top) else None
         common = {"kernel": top, "traffic": traffic, "launches_per_step": n / len(times), "ms_per_launch": ms / n,
                   "share_of_step": ms / sum(times)}
         if top in stored_bytes:

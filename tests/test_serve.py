@@ -91,16 +91,23 @@ def test_server_admits_one_oversized_request_alone():
 @pytest.mark.gpu
 def test_served_results_match_solo_runs():
     """Each request gives the same energy and forces in the concurrent mix (4 slots, shared
-    GPU, warm starts) as alone on a fresh context from a zero start: 1e-6 relative energy,
-    1e-5 relative force norm (both within the mixed form's 1e-8 solver tolerance)."""
+    GPU) as alone on a fresh context from a zero start, and a perturbed request warm-started
+    from its parent's solutions gives them too: 1e-6 relative energy, 1e-5 relative force
+    norm (both within the mixed form's 1e-8 solver tolerance)."""
     torch = pytest.importorskip("torch")
     reqs = serve.make_requests(4, rate=40.0, duration=0.4, size_min=20, size_max=120)
+    assert any(q.parent is not None for q in reqs)
     eng = serve.gpu_engine()
     res, _ = serve.Server(eng, slots=4, hbm_budget=64 * 2 ** 30).run(reqs)
     assert all("error" not in r.extra for r in res)
-    assert sum(r.warm for r in res) >= 1
+    solo = {}
     for q, r in zip(reqs, res):
-        e, f, _, _ = eng(q, None)
+        e, f, handle, _ = eng(q, None)
+        solo[q.rid] = handle
         assert abs(r.energy - e) <= 1e-6 * abs(e)
         assert np.linalg.norm(r.forces - f) <= 1e-5 * np.linalg.norm(f)
+        if q.parent is not None:
+            ew, fw, _, _ = eng(q, solo[q.parent])
+            assert abs(ew - e) <= 1e-6 * abs(e)
+            assert np.linalg.norm(fw - f) <= 1e-5 * np.linalg.norm(f)
     torch.cuda.synchronize()
