@@ -43,6 +43,11 @@ HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + w
 # with the digest of the kernel's source text they were taken on; null once that text changes.
 NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2153989632, "digest": "95c4403a9005b218"}}
 # CUDA functions whose source text a timed kernel name stands for
+# every group of launches the library times at kernel_timing = 2 (setup and forces as one group each)
+BREAKDOWN_NAMES = ([b + sfx for b in ("ab_apply", "ab_transpose", "yukawa_pot", "yukawa_adj", "krylov_dot",
+                                      "krylov_update", "ab_project", "synthesis", "masked_analysis",
+                                      "coupling_projection", "store") for sfx in ("_f16", "_f32", "_f64")]
+                   + ["setup_f64", "forces_f64"])
 KERNEL_SOURCES = {"ab_apply_f32": ["k_ab_hits_stored"], "ab_apply_f16": ["half8_to_float", "k_ab_hits_half"],
                   "ab_transpose_f16": ["half8_to_float", "k_ab_transpose_half"]}
 
@@ -59,6 +64,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
+    ap.add_argument("--no-breakdown", action="store_true", help="skip the instrumented breakdown step")
     ap.add_argument("--no-fp64", action="store_true", help="skip the one-step FP64 comparison")
     ap.add_argument("--ops-only", action="store_true",
                     help="setup plus one application of each FP32 operator, then exit (for ncu captures)")
@@ -223,7 +229,8 @@ def main():
         x = torch.randn(ctx.nvec, dtype=torch.float64, device=dev)
         y = torch.empty_like(x)
         times = {}
-        for op, name in ((10, "AB32"), (11, "ABT32"), (12, "C32"), (13, "CT32"), (2, "AB64"), (4, "C64")):
+        for op, name in ((10, "AB32"), (11, "ABT32"), (16, "AB16"), (17, "ABT16"), (12, "C32"), (13, "CT32"),
+                         (2, "AB64"), (4, "C64")):
             ctx.apply(op, x, y)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -236,9 +243,9 @@ def main():
         ctx.close()
         return
 
-    def step(timing=False, options=None):
+    def step(timing=0, options=None):
         ctx = G.Context(cen, rad, chg, w["eps_solvent"], w["kappa"], w["lmax"], w["n_lebedev"],
-                        surface=w["surface"], stream=stream.cuda_stream, kernel_timing=1 if timing else 0,
+                        surface=w["surface"], stream=stream.cuda_stream, kernel_timing=int(timing),
                         **(options or opts))
         ctx.solve()
         ctx.adjoint()
@@ -258,7 +265,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        ctx = step(timing=True)
+        ctx = step(timing=1)
         ev1.record(stream)
         torch.cuda.synchronize()
         times.append(ev0.elapsed_time(ev1))
@@ -266,7 +273,7 @@ def main():
         infos.append(info)
         launches += info["kernel_launches"]
         for base in FLOPS_PER_UNIT:
-            for suf in ("_f32", "_f64"):
+            for suf in ("_f16", "_f32", "_f64"):
                 n, ms = ctx.kernel_time(base + suf)
                 if n:
                     a = kstats.setdefault(base + suf, [0, 0.0])
@@ -320,6 +327,29 @@ def main():
                 "energy_rel_diff_mixed_vs_fp64": abs(e_mixed - e64) / abs(e64),
                 "force_rel_diff_mixed_vs_fp64": float((f_mixed - f_out).norm() / f_out.norm())}
 
+    # breakdown of one more (untimed) step: CUDA events around every group of launches
+    breakdown = None
+    if rank == 0 and not args.no_breakdown:
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctx = step(timing=2)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        parts = {}
+        for name in BREAKDOWN_NAMES:
+            n, ms = ctx.kernel_time(name)
+            if n:
+                parts[name] = {"launches": n, "ms": round(ms, 2)}
+        ctx.close()
+        wall = ev0.elapsed_time(ev1)
+        busy = sum(v["ms"] for v in parts.values())
+        breakdown = {"step_ms": round(wall, 1), "timed_ms": round(busy, 1),
+                     "other_ms": round(wall - busy, 1), "parts": parts,
+                     "other": "launch gaps, host synchronisation and host work of the solver (GMRES "
+                              "least squares, convergence checks), small untimed kernels"}
+
     # roofline of the dominant instrumented kernel
     info = infos[-1]
     nb = (w["lmax"] + 1) ** 2
@@ -370,7 +400,7 @@ def main():
                            "tol": 1e-8, "gmres_restart": args.restart, "precond_tol": args.precond_tol,
                            "l2": "512 MB buffer written between timed steps; working set > L2",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "fp64_path": fp64,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "breakdown": breakdown, "fp64_path": fp64,
                 "cpu_baseline": cpu, "clocks": clocks,
                 "solver": {"outer": info["solve_iterations"], "adjoint_outer": info["adjoint_iterations"],
                            "refinement": info["refinement_steps"], "residual": info["solve_residual"],

@@ -72,12 +72,17 @@ typedef struct {
     double precond_tol;  /* relative tolerance of the inner A/B solves that apply the L_AB
                             preconditioner of Sec. 4 inside flexible GMRES; default 1e-3;
                             1.0 switches the preconditioner off (plain restarted GMRES) */
-    int kernel_timing;   /* nonzero: record CUDA events around every launch of the hot kernels
-                            (read with ddlpb_kernel_time); default 0 */
+    int kernel_timing;   /* 1: record CUDA events around every launch of the hot kernels (read
+                            with ddlpb_kernel_time); 2: also around every other group of
+                            launches (Krylov vector work, projections, forces, setup); default 0 */
     int precond_coupling; /* nonzero: the preconditioner also holds the coupling C1/C2 between
                             each sphere and its neighbours (sources j in N_i and i itself);
                             0: L_AB = diag(A, B) only, as in Sec. 4; default 0 (with an
                             iterative inner solve the near coupling slows convergence down) */
+    int precond_fp16;    /* nonzero: in the mixed-precision form, the inner A/B solves of the
+                            preconditioner stream an FP16 copy of the stored A/B basis (FP32
+                            arithmetic; an inexact preconditioner is allowed in flexible GMRES);
+                            0: they use the FP32 basis; no effect in the FP64 form; default 1 */
 } ddlpb_options;
 
 typedef struct {
@@ -164,6 +169,8 @@ DDLPB_API ddlpb_status ddlpb_energy_device(ddlpb_ctx* ctx, double* e);
  *   op = 5: y = [C1^T (x_r + x_e) ; C2^T (x_r + x_e)]
  *   op = 8..13: the same operators in the FP32 arithmetic of the mixed-precision
  *            form (inputs rounded to FP32, outputs widened to FP64)
+ *   op = 16, 17: ops 2 and 3 as the preconditioner of the mixed-precision form applies
+ *            them (FP16 stored basis, FP32 arithmetic; see precond_fp16)
  * Errors: DDLPB_EINVAL for any other op.
  */
 DDLPB_API ddlpb_status ddlpb_apply_device(ddlpb_ctx* ctx, int op, const double* x, double* y);

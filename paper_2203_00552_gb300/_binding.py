@@ -21,12 +21,15 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTCONV", 4: "ECUDA", 5: "EORD
 
 # Operators of ddlpb_apply_device
 OP_L, OP_LT, OP_AB, OP_ABT, OP_C, OP_CT = range(6)
+OP_FP32 = 8          # added to an op code: the FP32 operators of the mixed-precision form
+OP_AB_F16, OP_ABT_F16 = 16, 17   # A/B and transpose as the mixed-precision preconditioner applies them
 
 
 class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int), ("gmres_restart", C.c_int),
                 ("precision", C.c_int), ("fmm_order", C.c_int), ("cuda_stream", C.c_void_p),
-                ("precond_tol", C.c_double), ("kernel_timing", C.c_int), ("precond_coupling", C.c_int)]
+                ("precond_tol", C.c_double), ("kernel_timing", C.c_int), ("precond_coupling", C.c_int),
+                ("precond_fp16", C.c_int)]
 
 
 class Info(C.Structure):

@@ -4,6 +4,7 @@
 // forces).  Section / equation names below refer to that paper.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,6 +73,18 @@ struct OpSet {
     T* Rp = nullptr;        // [L+1][H]  i-ratio corrections, same order
     int* hps = nullptr;     // [H] point index of the stored hit
     int* hjs = nullptr;     // [H] neighbour sphere of the stored hit
+    // FP16 copy of the stored basis streamed by the inner solves of the mixed-precision
+    // preconditioner (FP32 set only), in the order of the transposed hit list: every
+    // target-sphere chunk padded to groups of 8 hits, coefficient-major [lm][8 G8], so that
+    // one 16-byte load holds one basis function at 8 hits of one neighbour
+    bool half_ready = false, half_tried = false;
+    long long G8 = 0;       // groups of 8 hits
+    __half* Bh = nullptr;   // [nb][8 G8]
+    __half* Rh = nullptr;   // [L+1][8 G8]
+    int* hp8 = nullptr;     // [8 G8] point index, -1 in the padding
+    int* gj = nullptr;      // [G8] neighbour sphere of the group
+    int* cg0 = nullptr;     // [n_chunks] first group of the chunk
+    int* cng = nullptr;     // [n_chunks] groups in the chunk
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -169,6 +182,7 @@ struct ddlpb_ctx {
     OpSet<float> f32;           // built on first use by the mixed-precision solve
     double centroid[3] = {0, 0, 0};
     std::map<std::string, KernelTimes> ktimes;
+    int timer_block = 0;        // open group timers (KernelTimer)
     float* f32_vec = nullptr;   // FP32 Krylov workspace
 };
 
@@ -221,20 +235,31 @@ static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) 
 struct KernelTimer {
     ddlpb_ctx* c;
     cudaEvent_t e1 = nullptr;
-    KernelTimer(ddlpb_ctx* ctx, const char* name, bool fp32) : c(ctx) {
-        if (!c->opt.kernel_timing) return;
+    bool group = false;
+    // level 1: the hot kernels (kernel_timing >= 1); level 2: every other group of launches
+    // (kernel_timing >= 2), for a full breakdown of a step.  A group timer (setup, forces)
+    // suppresses the timers nested in it, so that the recorded times add up.
+    KernelTimer(ddlpb_ctx* ctx, const char* name, bool fp32, int level = 1, bool grp = false)
+        : KernelTimer(ctx, std::string(name) + (fp32 ? "_f32" : "_f64"), level, grp) {}
+    KernelTimer(ddlpb_ctx* ctx, const std::string& full_name, int level = 1, bool grp = false) : c(ctx) {
+        if (c->opt.kernel_timing < level || c->timer_block > 0) return;
         cudaEvent_t e0;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
             e1 = nullptr;
             return;
         }
-        KernelTimes& k = c->ktimes[std::string(name) + (fp32 ? "_f32" : "_f64")];
+        KernelTimes& k = c->ktimes[full_name];
         k.ev.push_back(e0);
         k.ev.push_back(e1);
         cudaEventRecord(e0, c->stream);
+        if (grp) {
+            group = true;
+            ++c->timer_block;
+        }
     }
     ~KernelTimer() {
         if (e1) cudaEventRecord(e1, c->stream);
+        if (group) --c->timer_block;
     }
 };
 
@@ -474,6 +499,9 @@ template <typename T> ddlpb_status op_apply_L_T(ddlpb_ctx* c, OpSet<T>& S, const
 template <typename T>
 ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE);
 template <typename T> ddlpb_status op_apply_P_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose);
+// The A/B operator of the preconditioner's inner solves: the FP16 stored basis for the FP32
+// set when ddlpb_options.precond_fp16 is set, otherwise op_apply_AB_T.
+template <typename T> ddlpb_status op_apply_AB_precond(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose);
 ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const double* radii,
                                   const double* charges, bool device_ptrs, int surface);
 ddlpb_status op_apply_L(ddlpb_ctx* c, const double* x, double* y, bool transpose);

@@ -236,32 +236,41 @@ __global__ void k_store_keys(int H, int N, const int* __restrict__ hp, const uns
     val[h] = h;
 }
 
-template <typename T, typename V4>
-__global__ void k_ab_store(int H, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
+template <typename O> __device__ __forceinline__ O to_store(float v);
+template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <typename O> __device__ __forceinline__ O to_store(double v) { return (O)v; }
+
+// Source position s in [0, H) takes hit order[s] and writes its row at dst[s] (s itself when
+// dst is null) of arrays with row stride `stride`; hps / hjs (when not null) get the hit's
+// point and neighbour sphere at that position.
+template <typename T, typename V4, typename O>
+__global__ void k_ab_store(int H, long long stride, int N, int nb, int L, T kappa, const V4* __restrict__ sph,
                            const V4* __restrict__ leb, YTabT<T> yt, const int* __restrict__ order,
-                           const int* __restrict__ hp, const int* __restrict__ hj, const T* __restrict__ hw,
-                           const T* __restrict__ Sinv, T* __restrict__ Bp, T* __restrict__ Rp, int* __restrict__ hps,
-                           int* __restrict__ hjs) {
+                           const long long* __restrict__ dst, const int* __restrict__ hp, const int* __restrict__ hj,
+                           const T* __restrict__ hw, const T* __restrict__ Sinv, O* __restrict__ Bp,
+                           O* __restrict__ Rp, int* __restrict__ hps, int* __restrict__ hjs) {
     extern __shared__ unsigned char smraw[];
     T* sm = (T*)smraw;
     const int bd = blockDim.x, tid = threadIdx.x;
     T* rr = sm;
     T* ri = rr + (L + 1) * bd;
-    const long long h = (long long)blockIdx.x * bd + tid;   // storage position
-    if (h >= H) return;
-    const int hh = order[h];
+    const long long s = (long long)blockIdx.x * bd + tid;   // source position
+    if (s >= H) return;
+    const long long h = dst ? dst[s] : s;                   // storage position
+    const int hh = order[s];
     const int p = hp[hh], i = p / N, n = p % N, j = hj[hh];
-    hps[h] = p;
-    hjs[h] = j;
-    const V4 a = sph[i], s = leb[n], b = sph[j];
-    const T dx = a.x + a.w * s.x - b.x, dy = a.y + a.w * s.y - b.y, dz = a.z + a.w * s.z - b.z;
+    if (hps) hps[h] = p;
+    if (hjs) hjs[h] = j;
+    const V4 a = sph[i], q = leb[n], b = sph[j];
+    const T dx = a.x + a.w * q.x - b.x, dy = a.y + a.w * q.y - b.y, dz = a.z + a.w * q.z - b.z;
     const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
     const T w = hw[hh];
     radial<T>(0, L, rho, b.w, kappa, nullptr, rr + tid, nullptr, bd);
     radial<T>(1, L, rho, b.w, kappa, Sinv + (size_t)j * (L + 2), ri + tid, nullptr, bd);
-    for (int l = 0; l <= L; ++l) Rp[(size_t)l * H + h] = ri[tid + l * bd] / rr[tid + l * bd];
+    for (int l = 0; l <= L; ++l) Rp[(size_t)l * stride + h] = to_store<O>(ri[tid + l * bd] / rr[tid + l * bd]);
     ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
-                  [&](int idx, int l, T yv) { Bp[(size_t)idx * H + h] = w * rr[tid + l * bd] * yv; });
+                  [&](int idx, int l, T yv) { Bp[(size_t)idx * stride + h] = to_store<O>(w * rr[tid + l * bd] * yv); });
 }
 
 // Hit-parallel form of the stored A/B product, step 1: every thread takes hits in a grid
@@ -324,6 +333,168 @@ __global__ void k_ab_project(int M, int N, int nb, const V4* __restrict__ leb, c
     }
 }
 
+
+// ---------------------------------------------------------------- A and B, FP16 stored basis
+
+// FP16 copy of the stored basis for the inner solves of the mixed-precision preconditioner,
+// in the order of the transposed hit list: the hits of every target-sphere chunk (at most
+// DDLPB_TCHUNK hits, one neighbour j) padded to whole groups of 8, so that one 16-byte load
+// gives one basis function at 8 hits of one neighbour.  Both directions stream this copy.
+__global__ void k_chunk_groups(int n_chunks, const int* __restrict__ chunk_cnt, int* __restrict__ cng) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_chunks) cng[k] = (chunk_cnt[k] + 7) / 8;
+}
+
+// Storage position of every entry of the transposed hit list; the neighbour of every group.
+__global__ void k_chunk_positions(const int* __restrict__ chunk_j, const int* __restrict__ chunk_t0,
+                                  const int* __restrict__ chunk_cnt, const int* __restrict__ cg0,
+                                  const int* __restrict__ cng, long long* __restrict__ tpos, int* __restrict__ gj) {
+    const int k = blockIdx.x;
+    const int t0 = chunk_t0[k], cnt = chunk_cnt[k], g0 = cg0[k];
+    for (int u = threadIdx.x; u < cnt; u += blockDim.x) tpos[t0 + u] = 8LL * g0 + u;
+    for (int g = threadIdx.x; g < cng[k]; g += blockDim.x) gj[g0 + g] = chunk_j[k];
+}
+
+__device__ __forceinline__ void half8_to_float(const uint4 v, float* f) {
+    const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 t = __half22float2(h[k]);
+        f[2 * k] = t.x;
+        f[2 * k + 1] = t.y;
+    }
+}
+
+// Forward product: one thread per group of 8 hits (one neighbour j), FP32 accumulation;
+// adds omega u_j(x_i^n) of both blocks into the grid arrays gr, ge (zeroed before).
+__global__ void __launch_bounds__(256) k_ab_hits_half(int nb, int L, long long G8, const int* __restrict__ hp8,
+                                                      const int* __restrict__ gj, const uint4* __restrict__ Bh,
+                                                      const uint4* __restrict__ Rh, const float* __restrict__ xr,
+                                                      const float* __restrict__ xe, float* __restrict__ gr,
+                                                      float* __restrict__ ge) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G8) return;
+    const int j = gj[g];
+    const float* Xr = xr + (size_t)j * nb;
+    const float* Xe = xe + (size_t)j * nb;
+    float ur[8], ue[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ur[k] = ue[k] = 0.f;
+    int idx = 0;
+    for (int l = 0; l <= L; ++l) {
+        float rat[8], pe[8];
+        half8_to_float(__ldcs(Rh + (size_t)l * G8 + g), rat);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pe[k] = 0.f;
+#pragma unroll 3
+        for (int m = 0; m <= 2 * l; ++m, ++idx) {
+            float b[8];
+            half8_to_float(__ldcs(Bh + (size_t)idx * G8 + g), b);
+            const float a = __ldg(Xr + idx), e = __ldg(Xe + idx);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                ur[k] = fmaf(b[k], a, ur[k]);
+                pe[k] = fmaf(b[k], e, pe[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ue[k] = fmaf(rat[k], pe[k], ue[k]);
+    }
+    const int4* P = reinterpret_cast<const int4*>(hp8) + 2 * g;
+    const int4 p0 = P[0], p1 = P[1];
+    const int p[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (p[k] >= 0) {
+            atomicAdd(gr + p[k], ur[k]);
+            atomicAdd(ge + p[k], ue[k]);
+        }
+}
+
+// Transposed product, the forward's mapping: one thread per group of 8 hits (consecutive lanes
+// read consecutive 16-byte pieces of a basis function), all basis functions in turn.  The
+// lanes of a warp holding the same neighbour j are contiguous; a segmented suffix sum over the
+// warp (5 shuffle steps, same-segment masks computed once) leaves every segment's sum in its
+// first lane, which adds it into acc (zeroed before) at sphere j.
+__global__ void __launch_bounds__(256) k_ab_transpose_half(int M, int nb, int L, long long G8,
+                                                           const int* __restrict__ gj, const int* __restrict__ hp8,
+                                                           const uint4* __restrict__ Bh,
+                                                           const uint4* __restrict__ Rh, const float* __restrict__ zr,
+                                                           const float* __restrict__ ze, float* __restrict__ acc) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool act = g < G8;
+    const int j = act ? gj[g] : -1;
+    unsigned same = 0;   // bit s: lane + 2^s holds the same neighbour
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int tj = __shfl_down_sync(FULL, j, 1 << s);
+        if (lane + (1 << s) < 32 && tj == j) same |= 1u << s;
+    }
+    const int jup = __shfl_up_sync(FULL, j, 1);   // every lane takes part in every shuffle
+    const bool head = act && (lane == 0 || jup != j);
+    float uR[8], uE[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) uR[q] = uE[q] = 0.f;
+    if (act) {
+        const int4* P = reinterpret_cast<const int4*>(hp8) + 2 * g;
+        const int4 p0 = P[0], p1 = P[1];
+        const int p[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (p[q] >= 0) {
+                uR[q] = zr[p[q]];
+                uE[q] = ze[p[q]];
+            }
+    }
+    float* accR = act ? acc + (size_t)j * nb : acc;
+    float* accE = act ? acc + (size_t)M * nb + (size_t)j * nb : acc;
+    int idx = 0;
+    for (int l = 0; l <= L; ++l) {
+        float w[8];
+        {
+            float rat[8];
+            if (act) {
+                half8_to_float(__ldcs(Rh + (size_t)l * G8 + g), rat);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) rat[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] = uE[q] * rat[q];
+        }
+#pragma unroll 3
+        for (int m = 0; m <= 2 * l; ++m, ++idx) {
+            float b[8];
+            if (act) {
+                half8_to_float(__ldcs(Bh + (size_t)idx * G8 + g), b);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b[q] = 0.f;
+            }
+            float vR = 0.f, vE = 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                vR = fmaf(b[q], uR[q], vR);
+                vE = fmaf(b[q], w[q], vE);
+            }
+#pragma unroll
+            for (int s = 0; s < 5; ++s) {
+                const float tR = __shfl_down_sync(FULL, vR, 1 << s);
+                const float tE = __shfl_down_sync(FULL, vE, 1 << s);
+                if (same & (1u << s)) {
+                    vR += tR;
+                    vE += tE;
+                }
+            }
+            if (head) {
+                atomicAdd(accR + idx, vR);
+                atomicAdd(accE + idx, vE);
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------- dense coupling (L_C)
 
@@ -709,6 +880,7 @@ ddlpb_status opset_prepare<float>(ddlpb_ctx* c, OpSet<float>& S) {
 template <typename T>
 static ddlpb_status build_stored(ddlpb_ctx* c, OpSet<T>& S) {
     S.store_tried = true;
+    KernelTimer kt(c, "store", sizeof(T) == 4, 2);
     const int N = c->N, nb = c->nb, L = c->lmax;
     const long long H = c->H;
     if (H <= 0) return DDLPB_OK;
@@ -730,10 +902,10 @@ static ddlpb_status build_stored(ddlpb_ctx* c, OpSet<T>& S) {
     DDLPB_TRY(ctx_alloc(c, &S.hps, H));
     DDLPB_TRY(ctx_alloc(c, &S.hjs, H));
     size_t smem = sizeof(T) * 2 * (size_t)(L + 1) * BLK;
-    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<T, typename OpSet<T>::V4>, smem));
-    k_ab_store<T><<<ceil_div(H, BLK), BLK, smem, c->stream>>>((int)H, N, nb, L, (T)c->kappa, S.sph, S.leb, S.yt,
-                                                             order, c->hit_p, c->hit_j, S.hit_w, S.Sinv, S.Bp, S.Rp,
-                                                             S.hps, S.hjs);
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<T, typename OpSet<T>::V4, T>, smem));
+    k_ab_store<T, typename OpSet<T>::V4, T><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
+        (int)H, H, N, nb, L, (T)c->kappa, S.sph, S.leb, S.yt, order, nullptr, c->hit_p, c->hit_j, S.hit_w, S.Sinv,
+        S.Bp, S.Rp, S.hps, S.hjs);
     DDLPB_LAUNCHED(c, "ab_store");
     S.stored = true;
     return DDLPB_OK;
@@ -742,6 +914,7 @@ static ddlpb_status build_stored(ddlpb_ctx* c, OpSet<T>& S) {
 template <typename T>
 static ddlpb_status synthesis_T(ddlpb_ctx* c, OpSet<T>& S, const T* coef, int rows, T* grid, bool weighted) {
     if (rows <= 0) return DDLPB_OK;
+    KernelTimer kt(c, "synthesis", sizeof(T) == 4, 2);
     k_synthesis<T><<<rows, BLK, sizeof(T) * c->nb, c->stream>>>(c->N, c->nb, S.YT, S.leb, coef, grid, weighted);
     DDLPB_LAUNCHED(c, "synthesis");
     return DDLPB_OK;
@@ -751,6 +924,7 @@ template <typename T>
 static ddlpb_status masked_analysis_T(ddlpb_ctx* c, OpSet<T>& S, const T* val_ext, T scale, const T* cik_scale,
                                       T* out, int out_stride, int accumulate) {
     size_t smem = (sizeof(T) + sizeof(int)) * c->N;
+    KernelTimer kt(c, "masked_analysis", sizeof(T) == 4, 2);
     k_masked_analysis<T><<<c->M, BLK, smem, c->stream>>>(c->N, c->nb, c->lmax, c->ext_ptr, c->ext_p, S.ext_x, S.leb,
                                                          S.Y, val_ext, scale, cik_scale, out, out_stride, accumulate);
     DDLPB_LAUNCHED(c, "masked_analysis");
@@ -775,9 +949,12 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
                                                                  x + (size_t)c->M * c->nb, S.gridA, S.gridB);
                 DDLPB_LAUNCHED(c, "ab_hits_stored");
             }
-            k_ab_project<T, V4><<<c->M, BLK, sizeof(T) * 2 * (size_t)c->N, c->stream>>>(c->M, c->N, c->nb, S.leb, S.Y,
-                                                                                       S.gridA, S.gridB, x, y);
-            DDLPB_LAUNCHED(c, "ab_project");
+            {
+                KernelTimer kt(c, "ab_project", sizeof(T) == 4, 2);
+                k_ab_project<T, V4><<<c->M, BLK, sizeof(T) * 2 * (size_t)c->N, c->stream>>>(c->M, c->N, c->nb, S.leb, S.Y,
+                                                                                           S.gridA, S.gridB, x, y);
+                DDLPB_LAUNCHED(c, "ab_project");
+            }
             return DDLPB_OK;
         }
     }
@@ -809,10 +986,107 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     return DDLPB_OK;
 }
 
+// FP16 copy of the stored basis (FP32 set), built on the first preconditioner application.
+static ddlpb_status build_half(ddlpb_ctx* c, OpSet<float>& S) {
+    S.half_tried = true;
+    KernelTimer kt(c, std::string("store_f16"), 2);
+    const long long H = c->H;
+    const int nch = c->n_chunks, nb = c->nb, L = c->lmax;
+    if (H <= 0 || nch <= 0) return DDLPB_OK;
+    DDLPB_TRY(ctx_alloc(c, &S.cng, nch));
+    DDLPB_TRY(ctx_alloc(c, &S.cg0, nch));
+    k_chunk_groups<<<ceil_div(nch, 256), 256, 0, c->stream>>>(nch, c->chunk_cnt, S.cng);
+    DDLPB_LAUNCHED(c, "chunk_groups");
+    size_t bytes = 0;
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(nullptr, bytes, S.cng, S.cg0, nch, c->stream));
+    void* tmp = nullptr;
+    DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(tmp, bytes, S.cng, S.cg0, nch, c->stream));
+    int last[2] = {0, 0};
+    DDLPB_CK(c, cudaMemcpyAsync(&last[0], S.cg0 + nch - 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DDLPB_CK(c, cudaMemcpyAsync(&last[1], S.cng + nch - 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    const long long G8 = (long long)last[0] + last[1];
+    const size_t H8 = 8 * (size_t)G8;
+    long long* tpos = nullptr;
+    DDLPB_TRY(ctx_alloc(c, &tpos, H));
+    DDLPB_TRY(ctx_alloc(c, &S.Bh, (size_t)nb * H8));
+    DDLPB_TRY(ctx_alloc(c, &S.Rh, (size_t)(L + 1) * H8));
+    DDLPB_TRY(ctx_alloc(c, &S.hp8, H8));
+    DDLPB_TRY(ctx_alloc(c, &S.gj, (size_t)G8));
+    DDLPB_CK(c, cudaMemsetAsync(S.Bh, 0, sizeof(__half) * nb * H8, c->stream));
+    DDLPB_CK(c, cudaMemsetAsync(S.Rh, 0, sizeof(__half) * (L + 1) * H8, c->stream));
+    DDLPB_CK(c, cudaMemsetAsync(S.hp8, 0xFF, sizeof(int) * H8, c->stream));
+    k_chunk_positions<<<nch, 128, 0, c->stream>>>(c->chunk_j, c->chunk_t0, c->chunk_cnt, S.cg0, S.cng, tpos, S.gj);
+    DDLPB_LAUNCHED(c, "chunk_positions");
+    size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<float, float4, __half>, smem));
+    k_ab_store<float, float4, __half><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
+        (int)H, (long long)H8, c->N, nb, L, (float)c->kappa, S.sph, S.leb, S.yt, c->thit_h, tpos, c->hit_p, c->hit_j,
+        S.hit_w, S.Sinv, S.Bh, S.Rh, S.hp8, nullptr);
+    DDLPB_LAUNCHED(c, "ab_store_half");
+    S.G8 = G8;
+    S.half_ready = true;
+    return DDLPB_OK;
+}
+
+// A/B (or their transposes) with the FP16 stored basis, FP32 vectors.
+static ddlpb_status apply_AB_half(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose) {
+    DDLPB_TRY(opset_prepare<float>(c, S));
+    if (!S.half_tried) DDLPB_TRY(build_half(c, S));
+    if (!S.half_ready) return op_apply_AB_T<float>(c, S, x, y, transpose, nullptr, nullptr);
+    const int M = c->M, nb = c->nb, L = c->lmax;
+    const float* xe = x + (size_t)M * nb;
+    if (!transpose) {
+        const long long MN = (long long)M * c->N;
+        DDLPB_CK(c, cudaMemsetAsync(S.gridA, 0, sizeof(float) * MN, c->stream));
+        DDLPB_CK(c, cudaMemsetAsync(S.gridB, 0, sizeof(float) * MN, c->stream));
+        {
+            KernelTimer kt(c, std::string("ab_apply_f16"));
+            k_ab_hits_half<<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(nb, L, S.G8, S.hp8, S.gj, (const uint4*)S.Bh,
+                                                                        (const uint4*)S.Rh, x, xe, S.gridA, S.gridB);
+            DDLPB_LAUNCHED(c, "ab_hits_half");
+        }
+        {
+            KernelTimer kt(c, "ab_project", true, 2);
+            k_ab_project<float, float4><<<M, BLK, sizeof(float) * 2 * (size_t)c->N, c->stream>>>(M, c->N, nb, S.leb, S.Y,
+                                                                                                S.gridA, S.gridB, x, y);
+            DDLPB_LAUNCHED(c, "ab_project");
+        }
+        return DDLPB_OK;
+    }
+    DDLPB_TRY(synthesis_T<float>(c, S, x, M, S.gridA, true));
+    DDLPB_TRY(synthesis_T<float>(c, S, xe, M, S.gridB, true));
+    const long long nv = 2LL * M * nb;
+    DDLPB_CK(c, cudaMemsetAsync(S.acc, 0, sizeof(float) * nv, c->stream));
+    {
+        KernelTimer kt(c, std::string("ab_transpose_f16"));
+        k_ab_transpose_half<<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(M, nb, L, S.G8, S.gj, S.hp8, (const uint4*)S.Bh,
+                                                                         (const uint4*)S.Rh, S.gridA, S.gridB, S.acc);
+        DDLPB_LAUNCHED(c, "ab_transpose_half");
+    }
+    k_ab_transpose_finish<float><<<ceil_div(nv, 256), 256, 0, c->stream>>>(nv, x, S.acc, y);
+    DDLPB_LAUNCHED(c, "ab_transpose_finish");
+    return DDLPB_OK;
+}
+
+template <>
+ddlpb_status op_apply_AB_precond<double>(ddlpb_ctx* c, OpSet<double>& S, const double* x, double* y,
+                                         bool transpose) {
+    return op_apply_AB_T<double>(c, S, x, y, transpose, nullptr, nullptr);
+}
+
+template <>
+ddlpb_status op_apply_AB_precond<float>(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose) {
+    if (c->opt.precond_fp16) return apply_AB_half(c, S, x, y, transpose);
+    return op_apply_AB_T<float>(c, S, x, y, transpose, nullptr, nullptr);
+}
+
 template <typename T>
 static ddlpb_status source_mu_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* mu) {
     if (c->n_src == 0) return DDLPB_OK;
     size_t smem = sizeof(T) * (c->nb + c->N) + sizeof(int) * c->N;
+    KernelTimer kt(c, "coupling_projection", sizeof(T) == 4, 2);
     k_source_mu<T><<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, (T)(c->eps1 / c->eps2), c->src,
                                                        S.sph, S.di, S.cik, c->ext_ptr, c->ext_p, S.ext_x, S.leb, S.Y,
                                                        x, mu);
@@ -858,6 +1132,7 @@ static ddlpb_status yukawa_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* n
 
 template <typename T>
 static ddlpb_status ext_weights_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* cext) {
+    KernelTimer kt(c, "coupling_projection", sizeof(T) == 4, 2);
     k_ext_weights<T><<<c->M, BLK, sizeof(T) * c->nb, c->stream>>>(c->M, c->N, c->nb, c->ext_ptr, c->ext_p, S.ext_x,
                                                                   S.leb, S.Y, x, cext);
     DDLPB_LAUNCHED(c, "ext_weights");
@@ -1004,6 +1279,8 @@ ddlpb_status op_apply_fp32(ddlpb_ctx* c, int op, const double* x, double* y) {
         case 3: DDLPB_TRY(op_apply_AB_T<float>(c, c->f32, xf, yf, true, nullptr, nullptr)); break;
         case 4: DDLPB_TRY(apply_C_T<float>(c, c->f32, xf, yf, false, false)); break;
         case 5: DDLPB_TRY(apply_C_T<float>(c, c->f32, xf, yf, true, false)); break;
+        case 8: DDLPB_TRY(apply_AB_half(c, c->f32, xf, yf, false)); break;
+        case 9: DDLPB_TRY(apply_AB_half(c, c->f32, xf, yf, true)); break;
         default: c->err = "bad operator"; return DDLPB_EINVAL;
     }
     k_convert<float, double><<<ceil_div(n, 256), 256, 0, c->stream>>>(n, yf, y);

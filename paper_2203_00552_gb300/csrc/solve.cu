@@ -27,31 +27,38 @@ static bool trace_on() {
 }
 
 #define RBLK 256
-#define RGRID 592   // 4 x 148 resident CTAs
+#define RGRID 608   // 4 x 152 SMs
 #define VG 1184
 #define VB 256
 
 // partial[k * G + g] = sum over the g-th grid stride of V_k . w (accumulated in FP64)
+// Partial dot products <V_k, w>, k < kk: block b owns one contiguous slice of the rows for
+// all k; its warps take (k, sub-slice) tasks (sub-slices when kk is below the warp count),
+// lanes sum a few products in the vectors' precision, the lane sums are added in FP64.
 template <typename T>
-__global__ void k_multidot(long long n, int kk, const T* __restrict__ V, const T* __restrict__ w,
-                           double* __restrict__ partial) {
-    __shared__ double red[RBLK / 32];
-    const int k = blockIdx.y;
-    const T* v = V + (size_t)k * n;
-    double s = 0;
-    for (long long i = (long long)blockIdx.x * RBLK + threadIdx.x; i < n; i += (long long)gridDim.x * RBLK)
-        s += (double)v[i] * (double)w[i];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+__global__ void __launch_bounds__(RBLK) k_multidot(long long n, int kk, const T* __restrict__ V,
+                                                   const T* __restrict__ w, double* __restrict__ partial) {
+    extern __shared__ double sacc[];   // [kk]
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * per, i1 = i0 + per < n ? i0 + per : n;
+    for (int k = threadIdx.x; k < kk; k += RBLK) sacc[k] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0;
-        for (int q = 0; q < RBLK / 32; ++q) t += red[q];
-        partial[(size_t)k * gridDim.x + blockIdx.x] = t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = RBLK / 32;
+    const int P = kk < nw ? nw / kk : 1;
+    const long long len = i1 > i0 ? i1 - i0 : 0, plen = (len + P - 1) / P;
+    for (int t = warp; t < kk * P; t += nw) {
+        const int k = t / P, part = t % P;
+        const long long a = i0 + part * plen, b = a + plen < i1 ? a + plen : i1;
+        const T* v = V + (size_t)k * n;
+        T s = 0;
+#pragma unroll 4
+        for (long long i = a + lane; i < b; i += 32) s += v[i] * w[i];
+        const double d = warp_sum((double)s);
+        if (lane == 0) atomicAdd(&sacc[k], d);
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kk; k += RBLK) partial[(size_t)k * gridDim.x + blockIdx.x] = sacc[k];
 }
-
-// out[k] = (add ? out[k] : 0) + sum_g partial[k * G + g]; optional sqrt
 __global__ void k_reduce(int G, const double* __restrict__ partial, double* __restrict__ out, int add, int take_sqrt) {
     __shared__ double red[RBLK / 32];
     const int k = blockIdx.x;
@@ -181,8 +188,8 @@ static ddlpb_status krylov_alloc(ddlpb_ctx* c, Krylov<T>& K, int m, long long n,
 
 template <typename T>
 static ddlpb_status dots(ddlpb_ctx* c, Krylov<T>& K, int kk, const T* V, const T* w, double* out, bool sq) {
-    dim3 grid(RGRID, kk);
-    k_multidot<T><<<grid, RBLK, 0, c->stream>>>(K.n, kk, V, w, K.red);
+    KernelTimer kt(c, "krylov_dot", sizeof(T) == 4, 2);
+    k_multidot<T><<<RGRID, RBLK, sizeof(double) * kk, c->stream>>>(K.n, kk, V, w, K.red);
     DDLPB_LAUNCHED(c, "multidot");
     k_reduce<<<kk, RBLK, 0, c->stream>>>(RGRID, K.red, out, 0, sq ? 1 : 0);
     DDLPB_LAUNCHED(c, "reduce");
@@ -199,13 +206,14 @@ static ddlpb_status norm_host(ddlpb_ctx* c, Krylov<T>& K, const T* v, double* de
 }
 
 // Restarted (flexible) GMRES with classical Gram-Schmidt and one re-orthogonalisation
-// pass.  apply(in, out) is the operator, precond(in, out) the right preconditioner
+// pass (skipped when reorth is false: the few iterations of a loose inner solve).  apply(in, out) is the operator, precond(in, out) the right preconditioner
 // (used only when K.Z is set).  x holds the initial guess (all zero if x_zero).
 // Stops when the Krylov estimate of ||b - A x|| / ||b|| <= tol; the true residual
 // is recomputed at every restart.
 template <typename T, typename Apply, typename Prec>
 static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precond, const T* b, T* x, double tol,
-                            int maxit, bool x_zero, int* iters, double* rel_out, bool stall_exit = false) {
+                            int maxit, bool x_zero, int* iters, double* rel_out, bool stall_exit = false,
+                            bool reorth = true) {
     const long long n = K.n;
     const int m = K.m;
     cudaStream_t st = c->stream;
@@ -234,6 +242,7 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
             DDLPB_CK(c, cudaMemcpyAsync(K.r, b, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
         } else {
             DDLPB_TRY(apply(x, K.r));
+            KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
             k_axpby<T><<<VG, VB, 0, st>>>(n, 1.0, b, -1.0, K.r, K.r);
             DDLPB_LAUNCHED(c, "axpby");
         }
@@ -263,8 +272,11 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
             c->err = "GMRES reached max_iter (relative residual " + std::to_string(rel) + ")";
             return DDLPB_ENOTCONV;
         }
-        k_scale_by<T><<<VG, VB, 0, st>>>(n, K.r, nrm, K.V);
-        DDLPB_LAUNCHED(c, "scale");
+        {
+            KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
+            k_scale_by<T><<<VG, VB, 0, st>>>(n, K.r, nrm, K.V);
+            DDLPB_LAUNCHED(c, "scale");
+        }
         std::fill(gvec.begin(), gvec.end(), 0.0);
         gvec[0] = beta;
         int k = 0;
@@ -279,16 +291,25 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
                 DDLPB_TRY(apply(vk, K.w));
             }
             DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h1, false));
-            k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h1, K.w);
-            DDLPB_LAUNCHED(c, "sub_comb");
-            DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h2, false));
-            k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h2, K.w);
-            DDLPB_LAUNCHED(c, "sub_comb2");
-            k_add_vec<<<ceil_div(k + 1, 256), 256, 0, st>>>(k + 1, h2, h1);
-            DDLPB_LAUNCHED(c, "add_vec");
+            {
+                KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
+                k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h1, K.w);
+                DDLPB_LAUNCHED(c, "sub_comb");
+            }
+            if (reorth) {
+                DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h2, false));
+                KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
+                k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h2, K.w);
+                DDLPB_LAUNCHED(c, "sub_comb2");
+                k_add_vec<<<ceil_div(k + 1, 256), 256, 0, st>>>(k + 1, h2, h1);
+                DDLPB_LAUNCHED(c, "add_vec");
+            }
             DDLPB_TRY(dots<T>(c, K, 1, K.w, K.w, nrm, true));
-            k_scale_by<T><<<VG, VB, 0, st>>>(n, K.w, nrm, K.V + (size_t)(k + 1) * n);
-            DDLPB_LAUNCHED(c, "scale2");
+            {
+                KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
+                k_scale_by<T><<<VG, VB, 0, st>>>(n, K.w, nrm, K.V + (size_t)(k + 1) * n);
+                DDLPB_LAUNCHED(c, "scale2");
+            }
             DDLPB_CK(c, cudaMemcpyAsync(hp, h1, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
             DDLPB_CK(c, cudaMemcpyAsync(hp + (m + 2), nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
             DDLPB_CK(c, cudaStreamSynchronize(st));
@@ -322,8 +343,11 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
             yv[q] = s / H[(size_t)q * m + q];
         }
         DDLPB_CK(c, cudaMemcpyAsync(h2, yv.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-        k_add_combination<T><<<VG, VB, 0, st>>>(n, k, K.Z ? K.Z : K.V, h2, x);
-        DDLPB_LAUNCHED(c, "add_comb");
+        {
+            KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
+            k_add_combination<T><<<VG, VB, 0, st>>>(n, k, K.Z ? K.Z : K.V, h2, x);
+            DDLPB_LAUNCHED(c, "add_comb");
+        }
         DDLPB_CK(c, cudaStreamSynchronize(st));
     }
     *iters = total;
@@ -364,11 +388,12 @@ static ddlpb_status precond_apply(ddlpb_ctx* c, OpSet<T>& S, Krylov<T>& inner, b
     double rel = 0;
     auto ab = [&](const T* in, T* out) {
         if (c->opt.precond_coupling) return op_apply_P_T<T>(c, S, in, out, transpose);
-        return op_apply_AB_T<T>(c, S, in, out, transpose, nullptr, nullptr);
+        return op_apply_AB_precond<T>(c, S, in, out, transpose);
     };
     auto none = [&](const T*, T*) { return DDLPB_OK; };
     DDLPB_CK(c, cudaMemsetAsync(z, 0, sizeof(T) * inner.n, c->stream));
-    ddlpb_status s = gmres_T<T>(c, inner, ab, none, v, z, c->opt.precond_tol, kInnerMaxit, true, &it, &rel);
+    ddlpb_status s = gmres_T<T>(c, inner, ab, none, v, z, c->opt.precond_tol, kInnerMaxit, true, &it, &rel, false,
+                                c->opt.precond_tol < 1e-2);
     *inner_count += it;
     if (s == DDLPB_ENOTCONV) {
         c->err.clear();  // an inexact preconditioner is allowed in flexible GMRES
@@ -514,6 +539,7 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->precond_tol = 1e-3;
     o->kernel_timing = 0;
     o->precond_coupling = 0;
+    o->precond_fp16 = 1;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,
@@ -556,7 +582,11 @@ static ddlpb_status setup_common(int n, const double* centres, const double* rad
     c->opt = o;
     c->stream = (cudaStream_t)o.cuda_stream;
     cudaGetDevice(&c->device);
-    ddlpb_status s = ddlpb_internal_setup(c, centres, radii, charges, device, (int)surface);
+    ddlpb_status s;
+    {
+        KernelTimer kt(c, "setup", false, 2, true);
+        s = ddlpb_internal_setup(c, centres, radii, charges, device, (int)surface);
+    }
     if (s != DDLPB_OK) {
         g_setup_err = c->err;
         ddlpb_free(c);
@@ -641,7 +671,10 @@ extern "C" ddlpb_status ddlpb_forces_device(ddlpb_ctx* c, double* f) {
         c->err = "ddlpb_forces before a successful ddlpb_adjoint";
         return DDLPB_EORDER;
     }
-    DDLPB_TRY(compute_forces(c, f));
+    {
+        KernelTimer kt(c, "forces", false, 2, true);
+        DDLPB_TRY(compute_forces(c, f));
+    }
     DDLPB_CK(c, cudaStreamSynchronize(c->stream));
     return DDLPB_OK;
 }
@@ -654,14 +687,17 @@ extern "C" ddlpb_status ddlpb_forces(ddlpb_ctx* c, double* f) {
         return DDLPB_EORDER;
     }
     if (!c->force_acc) DDLPB_TRY(ctx_alloc(c, &c->force_acc, 3 * (size_t)c->M));
-    DDLPB_TRY(compute_forces(c, c->force_acc));
+    {
+        KernelTimer kt(c, "forces", false, 2, true);
+        DDLPB_TRY(compute_forces(c, c->force_acc));
+    }
     DDLPB_CK(c, cudaMemcpyAsync(f, c->force_acc, sizeof(double) * 3 * c->M, cudaMemcpyDeviceToHost, c->stream));
     DDLPB_CK(c, cudaStreamSynchronize(c->stream));
     return DDLPB_OK;
 }
 
 extern "C" ddlpb_status ddlpb_apply_device(ddlpb_ctx* c, int op, const double* x, double* y) {
-    if (!c || !x || !y || op < 0 || op > 13 || (op > 5 && op < 8)) return DDLPB_EINVAL;
+    if (!c || !x || !y || op < 0 || op > 17 || (op > 5 && op < 8) || (op > 13 && op < 16)) return DDLPB_EINVAL;
     c->err.clear();
     if (op >= 8) {
         DDLPB_TRY(op_apply_fp32(c, op - 8, x, y));

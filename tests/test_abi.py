@@ -63,6 +63,7 @@ def test_struct_layout_matches_header(tmp_path):
 def test_default_options(lib):
     o = _binding.default_options()
     assert o.eta == 0.1 and o.tol == 1e-8 and o.gmres_restart == 150 and o.fmm_order == 0
+    assert o.precond_fp16 == 1 and o.precond_coupling == 0
 
 
 def test_setup_rejects_bad_input_before_touching_the_gpu(lib):

@@ -230,6 +230,44 @@ def test_fp32_operators_track_fp64(case, op):
     assert float((y64 - y32).abs().max()) <= 1e-5 * scale
 
 
+def test_fp16_preconditioner_operators(case):
+    """A/B with the FP16 stored basis of the mixed-precision preconditioner: within 3e-3 of
+    the FP64 operators (FP16 rounding of the basis, 2^-11 relative), and the forward and
+    transposed kernels are exact transposes of each other (they stream the same FP16 values),
+    <A16 x, y> = <x, A16^T y> to FP32 accumulation accuracy."""
+    ctx = case["ctx"]
+    x = _rand(ctx.nvec, 21)
+    z = _rand(ctx.nvec, 22)
+    for op64, op16 in ((G.OP_AB, G.OP_AB_F16), (G.OP_ABT, G.OP_ABT_F16)):
+        y64 = torch.empty_like(x)
+        y16 = torch.empty_like(x)
+        ctx.apply(op64, x, y64)
+        ctx.apply(op16, x, y16)
+        assert float((y64 - y16).abs().max()) <= 3e-3 * float(y64.abs().max())
+    # the identity part (x itself) cancels in the transpose check: compare (I - A16) forms
+    ax = torch.empty_like(x)
+    atz = torch.empty_like(x)
+    ctx.apply(G.OP_AB_F16, x, ax)
+    ctx.apply(G.OP_ABT_F16, z, atz)
+    lhs = float(torch.dot(x - ax, z))
+    rhs = float(torch.dot(x, z - atz))
+    scale = float(torch.linalg.norm(x - ax) * torch.linalg.norm(z))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_mixed_with_fp32_preconditioner(case):
+    """The mixed form with the FP32 stored basis in the preconditioner (precond_fp16 = 0)
+    reaches the same energy as with the FP16 one."""
+    p = case["p"]
+    p.solve()
+    E_ref = p.energy()
+    for fp16 in (0, 1):
+        ctx = _ctx(case["c"], case["r"], case["q"], case["lmax"], case["n"], case["surf"], precision=G.DDLPB_MIXED,
+                   tol=1e-11, precond_fp16=fp16)
+        ctx.solve()
+        assert abs(ctx.energy() - E_ref) <= 1e-9 * abs(E_ref)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_gpu_kirkwood_tanford(precision):
     """The GPU path reproduces the Kirkwood-Tanford multipole energy and force of an
