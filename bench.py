@@ -41,7 +41,8 @@ FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_a
 HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
 # dram bytes per launch from the committed ncu capture (profiles/), keyed by (kernel, workload),
 # with the digest of the kernel's source text they were taken on; null once that text changes.
-NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2153989632, "digest": "95c4403a9005b218"}}
+NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2153989632, "digest": "95c4403a9005b218"},
+               ("ab_apply_f16", "globule1000_sas"): {"bytes_per_launch": 1085993728, "digest": "08d14d2dcb869bab"}}
 # CUDA functions whose source text a timed kernel name stands for
 # every group of launches the library times at kernel_timing = 2 (setup and forces as one group each)
 BREAKDOWN_NAMES = ([b + sfx for b in ("ab_apply", "ab_transpose", "yukawa_pot", "yukawa_adj", "krylov_dot",
