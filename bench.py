@@ -41,16 +41,18 @@ FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_a
 HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
 # dram bytes per launch from the committed ncu capture (profiles/), keyed by (kernel, workload),
 # with the digest of the kernel's source text they were taken on; null once that text changes.
-NCU_TRAFFIC = {("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2153989632, "digest": "95c4403a9005b218"},
-               ("ab_apply_f16", "globule1000_sas"): {"bytes_per_launch": 1085993728, "digest": "08d14d2dcb869bab"}}
+NCU_TRAFFIC = {("ab_transpose_f16", "globule1000_sas"): {"bytes_per_launch": 1081492992, "digest": "9b7ea5b416164da1"},
+               ("ab_apply_f32", "globule1000_sas"): {"bytes_per_launch": 2136090624, "digest": "0b867d54a8c164e3"}}
 # CUDA functions whose source text a timed kernel name stands for
+KERNEL_SOURCES = {"ab_apply_f32": ["load8_f", "load8", "k_ab_hits_chunk"],
+                  "ab_apply_f16": ["half8_to_float", "load8_h", "load8", "k_ab_hits_chunk"],
+                  "ab_transpose_f32": ["load8_f", "load8", "k_ab_transpose_chunk"],
+                  "ab_transpose_f16": ["half8_to_float", "load8_h", "load8", "k_ab_transpose_chunk"]}
 # every group of launches the library times at kernel_timing = 2 (setup and forces as one group each)
 BREAKDOWN_NAMES = ([b + sfx for b in ("ab_apply", "ab_transpose", "yukawa_pot", "yukawa_adj", "krylov_dot",
                                       "krylov_update", "ab_project", "synthesis", "masked_analysis",
                                       "coupling_projection", "store") for sfx in ("_f16", "_f32", "_f64")]
                    + ["setup_f64", "forces_f64"])
-KERNEL_SOURCES = {"ab_apply_f32": ["k_ab_hits_stored"], "ab_apply_f16": ["half8_to_float", "k_ab_hits_half"],
-                  "ab_transpose_f16": ["half8_to_float", "k_ab_transpose_half"]}
 
 
 def parse():
@@ -359,12 +361,11 @@ def main():
              "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
     roofline = None
     L = w["lmax"]
-    # The stored A/B products stream the basis (HBM-bound): algorithmic bytes per hit are the
-    # basis row (nb + lmax + 1 values) plus the hit's indices (point and sphere: 8 B in the FP32
-    # layout; the point alone in the FP16 layout, whose sphere is per group of 8 hits).
-    stored_bytes = {"ab_apply_f32": info["n_hits"] * ((nb + L + 1) * 4 + 8),
-                    "ab_apply_f16": info["n_hits"] * ((nb + L + 1) * 2 + 4),
-                    "ab_transpose_f16": info["n_hits"] * ((nb + L + 1) * 2 + 4)}
+    # The stored A/B products of the FP32 set stream the basis (HBM-bound): algorithmic bytes
+    # per hit are the basis row (nb + lmax + 1 values, 4 B in the FP32 copy, 2 B in the FP16
+    # copy) plus the hit's point index (4 B; its sphere is stored once per group of 8 hits).
+    stored_bytes = {k + sfx: info["n_hits"] * ((nb + L + 1) * w + 4)
+                    for k in ("ab_apply", "ab_transpose") for sfx, w in (("_f32", 4), ("_f16", 2))}
     if kstats:
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]

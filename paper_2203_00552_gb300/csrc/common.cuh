@@ -73,18 +73,21 @@ struct OpSet {
     T* Rp = nullptr;        // [L+1][H]  i-ratio corrections, same order
     int* hps = nullptr;     // [H] point index of the stored hit
     int* hjs = nullptr;     // [H] neighbour sphere of the stored hit
-    // FP16 copy of the stored basis streamed by the inner solves of the mixed-precision
-    // preconditioner (FP32 set only), in the order of the transposed hit list: every
-    // target-sphere chunk padded to groups of 8 hits, coefficient-major [lm][8 G8], so that
-    // one 16-byte load holds one basis function at 8 hits of one neighbour
-    bool half_ready = false, half_tried = false;
-    long long G8 = 0;       // groups of 8 hits
-    __half* Bh = nullptr;   // [nb][8 G8]
-    __half* Rh = nullptr;   // [L+1][8 G8]
-    int* hp8 = nullptr;     // [8 G8] point index, -1 in the padding
-    int* gj = nullptr;      // [G8] neighbour sphere of the group
-    int* cg0 = nullptr;     // [n_chunks] first group of the chunk
-    int* cng = nullptr;     // [n_chunks] groups in the chunk
+    // Chunk layout of the stored basis (FP32 set): the target-major hit list cut into chunks
+    // of one neighbour, each padded to whole groups of 8 hits, coefficient-major [lm][8 G8], so
+    // that one load holds one basis function at 8 hits of one neighbour.  Two copies: FP32
+    // (the outer products, both directions) and FP16 (the preconditioner's inner solves).
+    bool chunk_tried = false, chunk_ready = false;
+    long long G8 = 0;         // groups of 8 hits
+    long long* tpos = nullptr;  // [H] storage position of each entry of the target-major list
+    int* hp8 = nullptr;       // [8 G8] point index, -1 in the padding
+    int* gj = nullptr;        // [G8] neighbour sphere of the group
+    int* cg0 = nullptr;       // [n_chunks] first group of the chunk
+    int* cng = nullptr;       // [n_chunks] groups in the chunk
+    float* Bc = nullptr;      // [nb][8 G8]   FP32 copy
+    float* Rc = nullptr;      // [L+1][8 G8]
+    __half* Bh = nullptr;     // [nb][8 G8]   FP16 copy
+    __half* Rh = nullptr;     // [L+1][8 G8]
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -202,7 +205,7 @@ struct ddlpb_ctx {
         ++(ctx)->info.kernel_launches;                                             \
         cudaError_t e__ = cudaGetLastError();                                      \
         if (e__ != cudaSuccess) {                                                  \
-            (ctx)->err = std::string("launch ") + name + ": " + cudaGetErrorString(e__); \
+            (ctx)->err = std::string("launch ") + (name) + ": " + cudaGetErrorString(e__); \
             return DDLPB_ECUDA;                                                    \
         }                                                                          \
     } while (0)

@@ -12,6 +12,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -222,8 +223,9 @@ __global__ void k_ab_transpose_finish(long long n, const T* __restrict__ x, cons
 // Stored ("incore", Sec. 4) form of the sparse blocks A and B: for every hit h = (i, n, j)
 // the weighted basis omega_ij^eta r_l^j Y_lm^j at x_i^n and the i-ratio correction
 // rat_l = i_l(kappa rho)/i_l(kappa r_j) / (rho/r_j)^l are computed once at setup, in
-// coefficient-major layout [lm][H] (threads over hits read consecutive addresses).  The
-// transposes keep evaluating the basis on the fly (measured faster for the gather).
+// coefficient-major layout [lm][H] (threads over hits read consecutive addresses).  Used by
+// the FP64 set (the residuals of the mixed form and the FP64 form); its transposes evaluate
+// the basis on the fly.
 // Within each sphere the stored hits are ordered by neighbour j, then point n (order[k] is
 // the hit index h stored at position k), so that the threads of a warp mostly read the same
 // neighbour's coefficients.
@@ -334,12 +336,13 @@ __global__ void k_ab_project(int M, int N, int nb, const V4* __restrict__ leb, c
 }
 
 
-// ---------------------------------------------------------------- A and B, FP16 stored basis
+// ---------------------------------------------------------------- A and B, chunk layout (FP32 set)
 
-// FP16 copy of the stored basis for the inner solves of the mixed-precision preconditioner,
-// in the order of the transposed hit list: the hits of every target-sphere chunk (at most
-// DDLPB_TCHUNK hits, one neighbour j) padded to whole groups of 8, so that one 16-byte load
-// gives one basis function at 8 hits of one neighbour.  Both directions stream this copy.
+// Chunk layout of the stored basis (FP32 set), in the order of the transposed hit list: the
+// hits of every target-sphere chunk (at most DDLPB_TCHUNK hits, one neighbour j) padded to
+// whole groups of 8, so that one load gives one basis function at 8 hits of one neighbour
+// (16 bytes in the FP16 copy of the preconditioner, 32 in the FP32 copy of the outer
+// products).  Both directions stream the same copy.
 __global__ void k_chunk_groups(int n_chunks, const int* __restrict__ chunk_cnt, int* __restrict__ cng) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n_chunks) cng[k] = (chunk_cnt[k] + 7) / 8;
@@ -355,6 +358,13 @@ __global__ void k_chunk_positions(const int* __restrict__ chunk_j, const int* __
     for (int g = threadIdx.x; g < cng[k]; g += blockDim.x) gj[g0 + g] = chunk_j[k];
 }
 
+// Point index of every stored position (the padding keeps -1).
+__global__ void k_chunk_points(long long H, const long long* __restrict__ tpos, const int* __restrict__ tp,
+                               int* __restrict__ hp8) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < H) hp8[tpos[t]] = tp[t];
+}
+
 __device__ __forceinline__ void half8_to_float(const uint4 v, float* f) {
     const __half2* h = reinterpret_cast<const __half2*>(&v);
 #pragma unroll
@@ -365,11 +375,33 @@ __device__ __forceinline__ void half8_to_float(const uint4 v, float* f) {
     }
 }
 
+// 8 consecutive stored values (one basis function at the 8 hits of group q), as floats.
+__device__ __forceinline__ void load8_h(const __half* base, size_t q, float* f) {
+    half8_to_float(__ldcs(reinterpret_cast<const uint4*>(base) + q), f);
+}
+
+__device__ __forceinline__ void load8_f(const float* base, size_t q, float* f) {
+    const float4* p = reinterpret_cast<const float4*>(base) + 2 * q;
+    const float4 a = __ldcs(p), b = __ldcs(p + 1);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+}
+
+template <typename S>
+__device__ __forceinline__ void load8(const S* base, size_t q, float* f) {
+    if constexpr (std::is_same<S, __half>::value) {
+        load8_h(base, q, f);
+    } else {
+        load8_f(base, q, f);
+    }
+}
+
 // Forward product: one thread per group of 8 hits (one neighbour j), FP32 accumulation;
 // adds omega u_j(x_i^n) of both blocks into the grid arrays gr, ge (zeroed before).
-__global__ void __launch_bounds__(256) k_ab_hits_half(int nb, int L, long long G8, const int* __restrict__ hp8,
-                                                      const int* __restrict__ gj, const uint4* __restrict__ Bh,
-                                                      const uint4* __restrict__ Rh, const float* __restrict__ xr,
+// S: storage type of the basis copy (__half for the preconditioner, float for the outer products).
+template <typename S>
+__global__ void __launch_bounds__(256) k_ab_hits_chunk(int nb, int L, long long G8, const int* __restrict__ hp8,
+                                                       const int* __restrict__ gj, const S* __restrict__ Bh,
+                                                       const S* __restrict__ Rh, const float* __restrict__ xr,
                                                       const float* __restrict__ xe, float* __restrict__ gr,
                                                       float* __restrict__ ge) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,13 +415,13 @@ __global__ void __launch_bounds__(256) k_ab_hits_half(int nb, int L, long long G
     int idx = 0;
     for (int l = 0; l <= L; ++l) {
         float rat[8], pe[8];
-        half8_to_float(__ldcs(Rh + (size_t)l * G8 + g), rat);
+        load8(Rh, (size_t)l * G8 + g, rat);
 #pragma unroll
         for (int k = 0; k < 8; ++k) pe[k] = 0.f;
 #pragma unroll 3
         for (int m = 0; m <= 2 * l; ++m, ++idx) {
             float b[8];
-            half8_to_float(__ldcs(Bh + (size_t)idx * G8 + g), b);
+            load8(Bh, (size_t)idx * G8 + g, b);
             const float a = __ldg(Xr + idx), e = __ldg(Xe + idx);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -416,10 +448,11 @@ __global__ void __launch_bounds__(256) k_ab_hits_half(int nb, int L, long long G
 // lanes of a warp holding the same neighbour j are contiguous; a segmented suffix sum over the
 // warp (5 shuffle steps, same-segment masks computed once) leaves every segment's sum in its
 // first lane, which adds it into acc (zeroed before) at sphere j.
-__global__ void __launch_bounds__(256) k_ab_transpose_half(int M, int nb, int L, long long G8,
-                                                           const int* __restrict__ gj, const int* __restrict__ hp8,
-                                                           const uint4* __restrict__ Bh,
-                                                           const uint4* __restrict__ Rh, const float* __restrict__ zr,
+template <typename S>
+__global__ void __launch_bounds__(256) k_ab_transpose_chunk(int M, int nb, int L, long long G8,
+                                                            const int* __restrict__ gj, const int* __restrict__ hp8,
+                                                            const S* __restrict__ Bh, const S* __restrict__ Rh,
+                                                            const float* __restrict__ zr,
                                                            const float* __restrict__ ze, float* __restrict__ acc) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned FULL = 0xffffffffu;
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(256) k_ab_transpose_half(int M, int nb, int L,
         {
             float rat[8];
             if (act) {
-                half8_to_float(__ldcs(Rh + (size_t)l * G8 + g), rat);
+                load8(Rh, (size_t)l * G8 + g, rat);
             } else {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) rat[q] = 0.f;
@@ -468,7 +501,7 @@ __global__ void __launch_bounds__(256) k_ab_transpose_half(int M, int nb, int L,
         for (int m = 0; m <= 2 * l; ++m, ++idx) {
             float b[8];
             if (act) {
-                half8_to_float(__ldcs(Bh + (size_t)idx * G8 + g), b);
+                load8(Bh, (size_t)idx * G8 + g, b);
             } else {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) b[q] = 0.f;
@@ -931,10 +964,21 @@ static ddlpb_status masked_analysis_T(ddlpb_ctx* c, OpSet<T>& S, const T* val_ex
     return DDLPB_OK;
 }
 
+static ddlpb_status apply_AB_chunks(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose,
+                                    bool fp16, bool* done);
+
 template <typename T>
 ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, T* gridR, T* gridE) {
     DDLPB_TRY(opset_prepare<T>(c, S));
     const int L = c->lmax;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 set: both directions stream the FP32 copy in the chunk layout
+        if (y && !gridR) {
+            bool done = false;
+            DDLPB_TRY(apply_AB_chunks(c, S, x, y, transpose, false, &done));
+            if (done) return DDLPB_OK;
+        }
+    }
     if (!transpose && y && !gridR && !S.store_tried) DDLPB_TRY(build_stored<T>(c, S));
     if (S.stored && !gridR && y && !transpose) {
         using V4 = typename OpSet<T>::V4;
@@ -986,12 +1030,12 @@ ddlpb_status op_apply_AB_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool tra
     return DDLPB_OK;
 }
 
-// FP16 copy of the stored basis (FP32 set), built on the first preconditioner application.
-static ddlpb_status build_half(ddlpb_ctx* c, OpSet<float>& S) {
-    S.half_tried = true;
-    KernelTimer kt(c, std::string("store_f16"), 2);
+// Chunk layout of the stored basis (FP32 set): the target-major hit list cut into chunks of
+// one neighbour, each padded to whole groups of 8 hits; built on the first stored product.
+static ddlpb_status build_chunk_layout(ddlpb_ctx* c, OpSet<float>& S) {
+    S.chunk_tried = true;
     const long long H = c->H;
-    const int nch = c->n_chunks, nb = c->nb, L = c->lmax;
+    const int nch = c->n_chunks;
     if (H <= 0 || nch <= 0) return DDLPB_OK;
     DDLPB_TRY(ctx_alloc(c, &S.cng, nch));
     DDLPB_TRY(ctx_alloc(c, &S.cg0, nch));
@@ -1006,35 +1050,47 @@ static ddlpb_status build_half(ddlpb_ctx* c, OpSet<float>& S) {
     DDLPB_CK(c, cudaMemcpyAsync(&last[0], S.cg0 + nch - 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DDLPB_CK(c, cudaMemcpyAsync(&last[1], S.cng + nch - 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     DDLPB_CK(c, cudaStreamSynchronize(c->stream));
-    const long long G8 = (long long)last[0] + last[1];
-    const size_t H8 = 8 * (size_t)G8;
-    long long* tpos = nullptr;
-    DDLPB_TRY(ctx_alloc(c, &tpos, H));
-    DDLPB_TRY(ctx_alloc(c, &S.Bh, (size_t)nb * H8));
-    DDLPB_TRY(ctx_alloc(c, &S.Rh, (size_t)(L + 1) * H8));
+    S.G8 = (long long)last[0] + last[1];
+    const size_t H8 = 8 * (size_t)S.G8;
+    DDLPB_TRY(ctx_alloc(c, &S.tpos, H));
     DDLPB_TRY(ctx_alloc(c, &S.hp8, H8));
-    DDLPB_TRY(ctx_alloc(c, &S.gj, (size_t)G8));
-    DDLPB_CK(c, cudaMemsetAsync(S.Bh, 0, sizeof(__half) * nb * H8, c->stream));
-    DDLPB_CK(c, cudaMemsetAsync(S.Rh, 0, sizeof(__half) * (L + 1) * H8, c->stream));
+    DDLPB_TRY(ctx_alloc(c, &S.gj, (size_t)S.G8));
     DDLPB_CK(c, cudaMemsetAsync(S.hp8, 0xFF, sizeof(int) * H8, c->stream));
-    k_chunk_positions<<<nch, 128, 0, c->stream>>>(c->chunk_j, c->chunk_t0, c->chunk_cnt, S.cg0, S.cng, tpos, S.gj);
+    k_chunk_positions<<<nch, 128, 0, c->stream>>>(c->chunk_j, c->chunk_t0, c->chunk_cnt, S.cg0, S.cng, S.tpos, S.gj);
     DDLPB_LAUNCHED(c, "chunk_positions");
-    size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
-    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<float, float4, __half>, smem));
-    k_ab_store<float, float4, __half><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
-        (int)H, (long long)H8, c->N, nb, L, (float)c->kappa, S.sph, S.leb, S.yt, c->thit_h, tpos, c->hit_p, c->hit_j,
-        S.hit_w, S.Sinv, S.Bh, S.Rh, S.hp8, nullptr);
-    DDLPB_LAUNCHED(c, "ab_store_half");
-    S.G8 = G8;
-    S.half_ready = true;
+    k_chunk_points<<<ceil_div(H, 256), 256, 0, c->stream>>>(H, S.tpos, c->thit_p, S.hp8);
+    DDLPB_LAUNCHED(c, "chunk_points");
+    S.chunk_ready = true;
     return DDLPB_OK;
 }
 
-// A/B (or their transposes) with the FP16 stored basis, FP32 vectors.
-static ddlpb_status apply_AB_half(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose) {
-    DDLPB_TRY(opset_prepare<float>(c, S));
-    if (!S.half_tried) DDLPB_TRY(build_half(c, S));
-    if (!S.half_ready) return op_apply_AB_T<float>(c, S, x, y, transpose, nullptr, nullptr);
+// One copy of the basis in the chunk layout: O = float (outer products) or __half
+// (preconditioner).
+template <typename O>
+static ddlpb_status build_chunk_copy(ddlpb_ctx* c, OpSet<float>& S, O** Bc, O** Rc) {
+    const bool half = std::is_same<O, __half>::value;
+    KernelTimer kt(c, std::string(half ? "store_f16" : "store_f32"), 2);
+    const long long H = c->H;
+    const int nb = c->nb, L = c->lmax;
+    const size_t H8 = 8 * (size_t)S.G8;
+    DDLPB_TRY(ctx_alloc(c, Bc, (size_t)nb * H8));
+    DDLPB_TRY(ctx_alloc(c, Rc, (size_t)(L + 1) * H8));
+    DDLPB_CK(c, cudaMemsetAsync(*Bc, 0, sizeof(O) * nb * H8, c->stream));
+    DDLPB_CK(c, cudaMemsetAsync(*Rc, 0, sizeof(O) * (L + 1) * H8, c->stream));
+    size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<float, float4, O>, smem));
+    k_ab_store<float, float4, O><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
+        (int)H, (long long)H8, c->N, nb, L, (float)c->kappa, S.sph, S.leb, S.yt, c->thit_h, S.tpos, c->hit_p, c->hit_j,
+        S.hit_w, S.Sinv, *Bc, *Rc, nullptr, nullptr);
+    DDLPB_LAUNCHED(c, half ? "ab_store_half" : "ab_store_chunk");
+    return DDLPB_OK;
+}
+
+// A/B (or their transposes) with the basis copy in the chunk layout, FP32 vectors: the FP16
+// copy (fp16) or the FP32 one.  *done = false when there is no layout (no hits at all).
+template <typename O>
+static ddlpb_status apply_chunks(ddlpb_ctx* c, OpSet<float>& S, const O* Bc, const O* Rc, const char* tag,
+                                 const float* x, float* y, bool transpose) {
     const int M = c->M, nb = c->nb, L = c->lmax;
     const float* xe = x + (size_t)M * nb;
     if (!transpose) {
@@ -1042,10 +1098,10 @@ static ddlpb_status apply_AB_half(ddlpb_ctx* c, OpSet<float>& S, const float* x,
         DDLPB_CK(c, cudaMemsetAsync(S.gridA, 0, sizeof(float) * MN, c->stream));
         DDLPB_CK(c, cudaMemsetAsync(S.gridB, 0, sizeof(float) * MN, c->stream));
         {
-            KernelTimer kt(c, std::string("ab_apply_f16"));
-            k_ab_hits_half<<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(nb, L, S.G8, S.hp8, S.gj, (const uint4*)S.Bh,
-                                                                        (const uint4*)S.Rh, x, xe, S.gridA, S.gridB);
-            DDLPB_LAUNCHED(c, "ab_hits_half");
+            KernelTimer kt(c, std::string("ab_apply_") + tag);
+            k_ab_hits_chunk<O><<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(nb, L, S.G8, S.hp8, S.gj, Bc, Rc, x, xe,
+                                                                            S.gridA, S.gridB);
+            DDLPB_LAUNCHED(c, "ab_hits_chunk");
         }
         {
             KernelTimer kt(c, "ab_project", true, 2);
@@ -1060,14 +1116,39 @@ static ddlpb_status apply_AB_half(ddlpb_ctx* c, OpSet<float>& S, const float* x,
     const long long nv = 2LL * M * nb;
     DDLPB_CK(c, cudaMemsetAsync(S.acc, 0, sizeof(float) * nv, c->stream));
     {
-        KernelTimer kt(c, std::string("ab_transpose_f16"));
-        k_ab_transpose_half<<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(M, nb, L, S.G8, S.gj, S.hp8, (const uint4*)S.Bh,
-                                                                         (const uint4*)S.Rh, S.gridA, S.gridB, S.acc);
-        DDLPB_LAUNCHED(c, "ab_transpose_half");
+        KernelTimer kt(c, std::string("ab_transpose_") + tag);
+        k_ab_transpose_chunk<O><<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(M, nb, L, S.G8, S.gj, S.hp8, Bc, Rc,
+                                                                             S.gridA, S.gridB, S.acc);
+        DDLPB_LAUNCHED(c, "ab_transpose_chunk");
     }
     k_ab_transpose_finish<float><<<ceil_div(nv, 256), 256, 0, c->stream>>>(nv, x, S.acc, y);
     DDLPB_LAUNCHED(c, "ab_transpose_finish");
     return DDLPB_OK;
+}
+
+static ddlpb_status apply_AB_chunks(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose,
+                                    bool fp16, bool* done) {
+    *done = false;
+    DDLPB_TRY(opset_prepare<float>(c, S));
+    if (!S.chunk_tried) DDLPB_TRY(build_chunk_layout(c, S));
+    if (!S.chunk_ready) return DDLPB_OK;
+    if (fp16) {
+        if (!S.Bh) DDLPB_TRY(build_chunk_copy<__half>(c, S, &S.Bh, &S.Rh));
+        DDLPB_TRY(apply_chunks<__half>(c, S, S.Bh, S.Rh, "f16", x, y, transpose));
+    } else {
+        if (!S.Bc) DDLPB_TRY(build_chunk_copy<float>(c, S, &S.Bc, &S.Rc));
+        DDLPB_TRY(apply_chunks<float>(c, S, S.Bc, S.Rc, "f32", x, y, transpose));
+    }
+    *done = true;
+    return DDLPB_OK;
+}
+
+// A/B (or their transposes) with the FP16 copy, FP32 vectors (FP32 products when there are no hits).
+static ddlpb_status apply_AB_half(ddlpb_ctx* c, OpSet<float>& S, const float* x, float* y, bool transpose) {
+    bool done = false;
+    DDLPB_TRY(apply_AB_chunks(c, S, x, y, transpose, true, &done));
+    if (done) return DDLPB_OK;
+    return op_apply_AB_T<float>(c, S, x, y, transpose, nullptr, nullptr);
 }
 
 template <>

@@ -150,6 +150,14 @@ def test_isolated_and_nested_spheres():
     assert abs(ctx.energy() - p.energy()) <= 1e-10 * abs(p.energy())
     ctx.adjoint()
     assert np.abs(ctx.forces() - p.forces()).max() <= 1e-8
+    # mixed precision with no hits at all (two far ions): the stored FP32/FP16 paths are empty
+    c2, r2, q2 = c[:2], r[:2], q[:2]
+    p2 = O.DDLPB(c2, r2, q2, EPS, KAPPA, 4, 50)
+    p2.solve()
+    m = _ctx(c2, r2, q2, 4, 50, precision=G.DDLPB_MIXED, tol=1e-12)
+    assert m.info()["n_hits"] == 0
+    m.solve()
+    assert abs(m.energy() - p2.energy()) <= 1e-10 * abs(p2.energy())
 
 
 def test_device_setup_and_outputs_match_host():
