@@ -340,12 +340,13 @@ __global__ void k_ab_project(int M, int N, int nb, const V4* __restrict__ leb, c
 
 // Chunk layout of the stored basis (FP32 set), in the order of the transposed hit list: the
 // hits of every target-sphere chunk (at most DDLPB_TCHUNK hits, one neighbour j) padded to
-// whole groups of 8, so that one load gives one basis function at 8 hits of one neighbour
+// an even number of groups of 8, so that one load gives one basis function at 8 hits of one
+// neighbour
 // (16 bytes in the FP16 copy of the preconditioner, 32 in the FP32 copy of the outer
 // products).  Both directions stream the same copy.
 __global__ void k_chunk_groups(int n_chunks, const int* __restrict__ chunk_cnt, int* __restrict__ cng) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n_chunks) cng[k] = (chunk_cnt[k] + 7) / 8;
+    if (k < n_chunks) cng[k] = 2 * ((chunk_cnt[k] + 15) / 16);   // an even number of groups
 }
 
 // Storage position of every entry of the transposed hit list; the neighbour of every group.
@@ -397,50 +398,59 @@ __device__ __forceinline__ void load8(const S* base, size_t q, float* f) {
 
 // Forward product: one thread per group of 8 hits (one neighbour j), FP32 accumulation;
 // adds omega u_j(x_i^n) of both blocks into the grid arrays gr, ge (zeroed before).
-// S: storage type of the basis copy (__half for the preconditioner, float for the outer products).
-template <typename S>
+// S: storage type of the basis copy (__half for the preconditioner, float for the outer
+// products); GP: groups of 8 hits per thread (consecutive groups of one neighbour: the chunks
+// hold an even number of groups), so that a thread loads 32 bytes per basis function.
+template <typename S, int GP>
 __global__ void __launch_bounds__(256) k_ab_hits_chunk(int nb, int L, long long G8, const int* __restrict__ hp8,
                                                        const int* __restrict__ gj, const S* __restrict__ Bh,
                                                        const S* __restrict__ Rh, const float* __restrict__ xr,
-                                                      const float* __restrict__ xe, float* __restrict__ gr,
-                                                      float* __restrict__ ge) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G8) return;
+                                                       const float* __restrict__ xe, float* __restrict__ gr,
+                                                       float* __restrict__ ge) {
+    constexpr int NH = 8 * GP;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G8 / GP) return;
+    const long long g = t * GP;
     const int j = gj[g];
     const float* Xr = xr + (size_t)j * nb;
     const float* Xe = xe + (size_t)j * nb;
-    float ur[8], ue[8];
+    float ur[NH], ue[NH];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ur[k] = ue[k] = 0.f;
+    for (int k = 0; k < NH; ++k) ur[k] = ue[k] = 0.f;
     int idx = 0;
     for (int l = 0; l <= L; ++l) {
-        float rat[8], pe[8];
-        load8(Rh, (size_t)l * G8 + g, rat);
+        float rat[NH], pe[NH];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) pe[k] = 0.f;
+        for (int u = 0; u < GP; ++u) load8(Rh, (size_t)l * G8 + g + u, rat + 8 * u);
+#pragma unroll
+        for (int k = 0; k < NH; ++k) pe[k] = 0.f;
 #pragma unroll 3
         for (int m = 0; m <= 2 * l; ++m, ++idx) {
-            float b[8];
-            load8(Bh, (size_t)idx * G8 + g, b);
+            float b[NH];
+#pragma unroll
+            for (int u = 0; u < GP; ++u) load8(Bh, (size_t)idx * G8 + g + u, b + 8 * u);
             const float a = __ldg(Xr + idx), e = __ldg(Xe + idx);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < NH; ++k) {
                 ur[k] = fmaf(b[k], a, ur[k]);
                 pe[k] = fmaf(b[k], e, pe[k]);
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) ue[k] = fmaf(rat[k], pe[k], ue[k]);
+        for (int k = 0; k < NH; ++k) ue[k] = fmaf(rat[k], pe[k], ue[k]);
     }
     const int4* P = reinterpret_cast<const int4*>(hp8) + 2 * g;
-    const int4 p0 = P[0], p1 = P[1];
-    const int p[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (p[k] >= 0) {
-            atomicAdd(gr + p[k], ur[k]);
-            atomicAdd(ge + p[k], ue[k]);
-        }
+    for (int v = 0; v < 2 * GP; ++v) {
+        const int4 pv = P[v];
+        const int p[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (p[k] >= 0) {
+                atomicAdd(gr + p[k], ur[4 * v + k]);
+                atomicAdd(ge + p[k], ue[4 * v + k]);
+            }
+    }
 }
 
 // Transposed product, the forward's mapping: one thread per group of 8 hits (consecutive lanes
@@ -448,16 +458,18 @@ __global__ void __launch_bounds__(256) k_ab_hits_chunk(int nb, int L, long long 
 // lanes of a warp holding the same neighbour j are contiguous; a segmented suffix sum over the
 // warp (5 shuffle steps, same-segment masks computed once) leaves every segment's sum in its
 // first lane, which adds it into acc (zeroed before) at sphere j.
-template <typename S>
+template <typename S, int GP>
 __global__ void __launch_bounds__(256) k_ab_transpose_chunk(int M, int nb, int L, long long G8,
                                                             const int* __restrict__ gj, const int* __restrict__ hp8,
                                                             const S* __restrict__ Bh, const S* __restrict__ Rh,
                                                             const float* __restrict__ zr,
-                                                           const float* __restrict__ ze, float* __restrict__ acc) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                                            const float* __restrict__ ze, float* __restrict__ acc) {
+    constexpr int NH = 8 * GP;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long g = t * GP;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool act = g < G8;
+    const bool act = t < G8 / GP;
     const int j = act ? gj[g] : -1;
     unsigned same = 0;   // bit s: lane + 2^s holds the same neighbour
 #pragma unroll
@@ -467,48 +479,53 @@ __global__ void __launch_bounds__(256) k_ab_transpose_chunk(int M, int nb, int L
     }
     const int jup = __shfl_up_sync(FULL, j, 1);   // every lane takes part in every shuffle
     const bool head = act && (lane == 0 || jup != j);
-    float uR[8], uE[8];
+    float uR[NH], uE[NH];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) uR[q] = uE[q] = 0.f;
+    for (int q = 0; q < NH; ++q) uR[q] = uE[q] = 0.f;
     if (act) {
         const int4* P = reinterpret_cast<const int4*>(hp8) + 2 * g;
-        const int4 p0 = P[0], p1 = P[1];
-        const int p[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (p[q] >= 0) {
-                uR[q] = zr[p[q]];
-                uE[q] = ze[p[q]];
-            }
+        for (int v = 0; v < 2 * GP; ++v) {
+            const int4 pv = P[v];
+            const int p[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (p[k] >= 0) {
+                    uR[4 * v + k] = zr[p[k]];
+                    uE[4 * v + k] = ze[p[k]];
+                }
+        }
     }
     float* accR = act ? acc + (size_t)j * nb : acc;
     float* accE = act ? acc + (size_t)M * nb + (size_t)j * nb : acc;
     int idx = 0;
     for (int l = 0; l <= L; ++l) {
-        float w[8];
+        float w[NH];
         {
-            float rat[8];
+            float rat[NH];
             if (act) {
-                load8(Rh, (size_t)l * G8 + g, rat);
+#pragma unroll
+                for (int u = 0; u < GP; ++u) load8(Rh, (size_t)l * G8 + g + u, rat + 8 * u);
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) rat[q] = 0.f;
+                for (int q = 0; q < NH; ++q) rat[q] = 0.f;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) w[q] = uE[q] * rat[q];
+            for (int q = 0; q < NH; ++q) w[q] = uE[q] * rat[q];
         }
 #pragma unroll 3
         for (int m = 0; m <= 2 * l; ++m, ++idx) {
-            float b[8];
+            float b[NH];
             if (act) {
-                load8(Bh, (size_t)idx * G8 + g, b);
+#pragma unroll
+                for (int u = 0; u < GP; ++u) load8(Bh, (size_t)idx * G8 + g + u, b + 8 * u);
             } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) b[q] = 0.f;
+                for (int q = 0; q < NH; ++q) b[q] = 0.f;
             }
             float vR = 0.f, vE = 0.f;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < NH; ++q) {
                 vR = fmaf(b[q], uR[q], vR);
                 vE = fmaf(b[q], w[q], vE);
             }
@@ -1088,9 +1105,13 @@ static ddlpb_status build_chunk_copy(ddlpb_ctx* c, OpSet<float>& S, O** Bc, O** 
 
 // A/B (or their transposes) with the basis copy in the chunk layout, FP32 vectors: the FP16
 // copy (fp16) or the FP32 one.  *done = false when there is no layout (no hits at all).
+// Groups of 8 hits per thread: one, except in the FP16 transpose, which takes two (half the
+// warp reductions per byte streamed).
 template <typename O>
 static ddlpb_status apply_chunks(ddlpb_ctx* c, OpSet<float>& S, const O* Bc, const O* Rc, const char* tag,
                                  const float* x, float* y, bool transpose) {
+    constexpr int GP = 1;
+    constexpr int GPT = std::is_same<O, __half>::value ? 2 : 1;
     const int M = c->M, nb = c->nb, L = c->lmax;
     const float* xe = x + (size_t)M * nb;
     if (!transpose) {
@@ -1099,8 +1120,8 @@ static ddlpb_status apply_chunks(ddlpb_ctx* c, OpSet<float>& S, const O* Bc, con
         DDLPB_CK(c, cudaMemsetAsync(S.gridB, 0, sizeof(float) * MN, c->stream));
         {
             KernelTimer kt(c, std::string("ab_apply_") + tag);
-            k_ab_hits_chunk<O><<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(nb, L, S.G8, S.hp8, S.gj, Bc, Rc, x, xe,
-                                                                            S.gridA, S.gridB);
+            k_ab_hits_chunk<O, GP><<<ceil_div(S.G8 / GP, 256), 256, 0, c->stream>>>(nb, L, S.G8, S.hp8, S.gj, Bc, Rc,
+                                                                                     x, xe, S.gridA, S.gridB);
             DDLPB_LAUNCHED(c, "ab_hits_chunk");
         }
         {
@@ -1117,8 +1138,9 @@ static ddlpb_status apply_chunks(ddlpb_ctx* c, OpSet<float>& S, const O* Bc, con
     DDLPB_CK(c, cudaMemsetAsync(S.acc, 0, sizeof(float) * nv, c->stream));
     {
         KernelTimer kt(c, std::string("ab_transpose_") + tag);
-        k_ab_transpose_chunk<O><<<ceil_div(S.G8, 256), 256, 0, c->stream>>>(M, nb, L, S.G8, S.gj, S.hp8, Bc, Rc,
-                                                                             S.gridA, S.gridB, S.acc);
+        k_ab_transpose_chunk<O, GPT><<<ceil_div(S.G8 / GPT, 256), 256, 0, c->stream>>>(M, nb, L, S.G8, S.gj, S.hp8,
+                                                                                        Bc, Rc, S.gridA, S.gridB,
+                                                                                        S.acc);
         DDLPB_LAUNCHED(c, "ab_transpose_chunk");
     }
     k_ab_transpose_finish<float><<<ceil_div(nv, 256), 256, 0, c->stream>>>(nv, x, S.acc, y);
