@@ -160,6 +160,23 @@ def test_isolated_and_nested_spheres():
     assert abs(m.energy() - p2.energy()) <= 1e-10 * abs(p2.energy())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_max_degree_parity(precision):
+    """The largest degree the library takes (lmax 16, 434-point grid, exact to degree 35) on a
+    3-atom chain: energy and forces match the oracle, FP64 and mixed."""
+    c, r, q = synth.molecule(3, 11, "chain")
+    p = O.DDLPB(c, r, q, EPS, KAPPA, 16, 434)
+    p.solve()
+    p.adjoint()
+    ctx = _ctx(c, r, q, 16, 434, precision=precision, tol=1e-12)
+    assert ctx.info()["n_hits"] > 0
+    ctx.solve()
+    assert abs(ctx.energy() - p.energy()) <= 1e-10 * abs(p.energy())
+    ctx.adjoint()
+    F, F_ref = ctx.forces(), p.forces()
+    assert np.abs(F - F_ref).max() <= 1e-8 * max(1.0, np.abs(F_ref).max())
+
+
 def test_device_setup_and_outputs_match_host():
     c, r, q = synth.molecule(12, 4, "chain")
     h = _ctx(c, r, q, 4, 50)

@@ -88,6 +88,18 @@ def test_server_admits_one_oversized_request_alone():
     assert eng.max_active == 1 and len(res) == len(reqs)
 
 
+def test_batch_all_present_at_start_and_slots_filled():
+    reqs = serve.make_batch(5, 24, 10, 40)
+    assert len(reqs) == 24 and all(r.arrival == 0.0 and r.parent is None for r in reqs)
+    assert [r.atoms for r in reqs] == [r.atoms for r in serve.make_batch(5, 24, 10, 40)]
+    eng = _Fake()
+    srv = serve.Server(eng, slots=4, hbm_budget=10 ** 15)
+    res, makespan = srv.run(reqs)
+    assert srv.peak_inflight == 4 and eng.max_active <= 4
+    assert sum("error" in r.extra for r in res) == 1   # the planted failure of request 5
+    assert serve.summary(res, makespan)["atoms_per_s"] > 0
+
+
 @pytest.mark.gpu
 def test_served_results_match_solo_runs():
     """Each request gives the same energy and forces in the concurrent mix (4 slots, shared
