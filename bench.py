@@ -169,6 +169,11 @@ def whole_job(atoms_per_rank, ms_local, world, dist=None, device="cpu"):
     return t_max, world * atoms_per_rank / (t_max / 1e3)
 
 
+def stored_bytes_names():
+    """Timed kernels whose roofline is HBM bytes of a stored basis."""
+    return {k + sfx for k in ("ab_apply", "ab_transpose") for sfx in ("_f32", "_f16")}
+
+
 def kernel_digest(kernel):
     """Digest of the source text (definition through its closing brace) of the CUDA functions
     behind a timed kernel name; None if a function is not found."""
@@ -363,8 +368,8 @@ def main():
     # The stored A/B products of the FP32 set stream the basis (HBM-bound): algorithmic bytes
     # per hit are the basis row (nb + lmax + 1 values, 4 B in the FP32 copy, 2 B in the FP16
     # copy) plus the hit's point index (4 B; its sphere is stored once per group of 8 hits).
-    stored_bytes = {k + sfx: info["n_hits"] * ((nb + L + 1) * w + 4)
-                    for k in ("ab_apply", "ab_transpose") for sfx, w in (("_f32", 4), ("_f16", 2))}
+    stored_bytes = {name: info["n_hits"] * ((nb + L + 1) * (4 if name.endswith("_f32") else 2) + 4)
+                    for name in stored_bytes_names()}
     if kstats:
         top = max(kstats, key=lambda k: kstats[k][1])
         n, ms = kstats[top]

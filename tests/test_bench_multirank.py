@@ -47,3 +47,14 @@ def test_whole_job_over_two_gloo_ranks():
 def test_whole_job_single_rank():
     import bench
     assert bench.whole_job(500, 250.0, 1) == (250.0, 2000.0)
+
+
+def test_kernel_source_map_resolves_and_traffic_is_current():
+    """Every timed kernel name that bench.py maps to CUDA source text resolves to functions that
+    exist, and every recorded ncu traffic figure belongs to the current text of its kernel."""
+    import bench
+    for name in bench.KERNEL_SOURCES:
+        assert bench.kernel_digest(name) is not None, name
+    for (name, _workload), rec in bench.NCU_TRAFFIC.items():
+        assert rec["digest"] == bench.kernel_digest(name), name
+        assert name in bench.stored_bytes_names()
