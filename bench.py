@@ -295,8 +295,10 @@ def main():
     ms_step = sum(times) / len(times)
     t_max, value = whole_job(M, ms_step, world, pg, dev)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    hc, hr, hq = w["centres"], w["radii"], w["charges"]
+    # end to end through the C ABI with host buffers (copies inside the timed region): the
+    # inputs sit in pinned host memory, the results come back to host arrays
+    hc, hr, hq = (torch.from_numpy(np.ascontiguousarray(w[k], dtype=np.float64)).pin_memory().numpy()
+                  for k in ("centres", "radii", "charges"))
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else args.steps
     e2e_times = []
     for _ in range(e2e_steps):
