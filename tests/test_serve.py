@@ -123,3 +123,12 @@ def test_served_results_match_solo_runs():
             assert abs(ew - e) <= 1e-6 * abs(e)
             assert np.linalg.norm(fw - f) <= 1e-5 * np.linalg.norm(f)
     torch.cuda.synchronize()
+
+
+def test_sweep_degree_table_matches_the_stored_rules():
+    """The (lmax, grid) sweep keeps only grids exact to degree 2 lmax; its degree table must be
+    that of the Lebedev rules themselves."""
+    from oracle import sph
+    from paper_2203_00552_gb300 import sweeps
+    for n, d in sweeps.DEGREE.items():
+        assert sph.lebedev(n)[2] == d, n
