@@ -177,6 +177,18 @@ def test_max_degree_parity(precision):
     assert np.abs(F - F_ref).max() <= 1e-8 * max(1.0, np.abs(F_ref).max())
 
 
+def test_high_degree_globule_parity():
+    """lmax 10 on a 30-atom globule (590 points), the degree at which the energy of these dense
+    globules starts to drift with lmax (a property of the discretisation, which the oracle
+    shows too): the GPU energy equals the oracle's dense solve to 1e-10 relative."""
+    c, r, q = synth.molecule(30, 3, "globule", None, "vdw")
+    p = O.DDLPB(c, r, q, EPS, KAPPA, 10, 590)
+    p.solve(dense=True)
+    ctx = _ctx(c, r, q, 10, 590, tol=1e-12, gmres_restart=300, max_iter=4000)
+    ctx.solve()
+    assert abs(ctx.energy() - p.energy()) <= 1e-10 * abs(p.energy())
+
+
 def test_device_setup_and_outputs_match_host():
     c, r, q = synth.molecule(12, 4, "chain")
     h = _ctx(c, r, q, 4, 50)
