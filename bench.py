@@ -116,10 +116,11 @@ def reference_arm(args, w):
 
 
 def clocks_start():
-    path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
-    os.makedirs(os.path.dirname(path), exist_ok=True)
+    """Sample SM clocks and throttle reasons every 200 ms into a temporary CSV (nvidia-smi)."""
+    import tempfile
+    fd, path = tempfile.mkstemp(prefix="ddlpb_clocks_", suffix=".csv")
+    f = os.fdopen(fd, "w")
     try:
-        f = open(path, "w")
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -127,7 +128,9 @@ def clocks_start():
                              stdout=f, stderr=subprocess.DEVNULL)
         return p, f, path
     except Exception:
-        return None, None, path
+        f.close()
+        os.remove(path)
+        return None, None, None
 
 
 def clocks_stop(p, f, path, dev_index):
@@ -153,6 +156,7 @@ def clocks_stop(p, f, path, dev_index):
         for k, v in zip(names, parts[5:9]):
             if v.lower().startswith("active"):
                 reasons.add(k)
+    os.remove(path)
     if not sm:
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
