@@ -110,7 +110,7 @@ class DDLPB:
     """
 
     def __init__(self, centres, radii, charges, eps_solvent, kappa, lmax, n_lebedev,
-                 surface="vdw", eta=0.1, eps_solute=1.0):
+                 surface="vdw", eta=0.1, eps_solute=1.0, fmm_order=0):
         self.x = np.array(centres, dtype=np.float64).reshape(-1, 3)
         r = np.array(radii, dtype=np.float64).reshape(-1)
         if surface == "sas":
@@ -126,6 +126,8 @@ class DDLPB:
         self.lmax = int(lmax)
         self.nb = sph.nbasis(lmax)
         self.eta = float(eta)
+        self.fmm_order = int(fmm_order)   # > 0: Yukawa far field by the tree of oracle/fmm.py
+        self._tree = None
         self.s, self.w, self.degree = sph.lebedev(n_lebedev)
         self.N = self.s.shape[0]
         self.Y = sph.ylm(self.lmax, self.s)                     # [N, nb], Y_lm(s_n)
@@ -298,12 +300,54 @@ class DDLPB:
         c1 = (self.eps1 / self.eps2) * self.lidx[None, :] / self.r[:, None]
         return c1 * Xr - self.lexpand(self.di) * Xe
 
+    # ---- FMM mode: the potential of the k-ratio multipoles at the points with chi > 0
+    def _fmm(self):
+        if self._tree is None:
+            from .fmm import YukawaTree
+            self._tree = YukawaTree(self.x, self.kappa, self.lmax, self.fmm_order)
+            self._ext = [np.nonzero(self.chi[i] > 0)[0] for i in range(self.M)]
+            self._targets = np.concatenate([self.pts[i][self._ext[i]] for i in range(self.M)])
+        return self._tree
+
+    def _potential(self, mu):
+        """phi[i, n] = sum_j k-ratio basis of j at x_i^n times mu_j, at the points with chi > 0
+        (zero elsewhere); by the tree when fmm_order > 0, else directly."""
+        phi = np.zeros((self.M, self.N))
+        if self.fmm_order > 0:
+            tree = self._fmm()
+            vals = tree.potential(mu / self.lexpand(self.k_r), self._targets)
+            o = 0
+            for i in range(self.M):
+                k = len(self._ext[i])
+                phi[i, self._ext[i]] = vals[o:o + k]
+                o += k
+            return phi
+        for i in range(self.M):
+            for j in range(self.M):
+                phi[i] += self.basis("k", j, self.pts[i]) @ mu[j]
+        return phi
+
+    def _potential_T(self, z):
+        """Transpose of _potential for z[M, N] (only the entries with chi > 0 count)."""
+        if self.fmm_order > 0:
+            tree = self._fmm()
+            zt = np.concatenate([z[i, self._ext[i]] for i in range(self.M)])
+            return tree.potential_T(zt, self._targets) / self.lexpand(self.k_r)
+        nu = np.zeros((self.M, self.nb))
+        for i in range(self.M):
+            for j in range(self.M):
+                nu[j] += z[i] @ self.basis("k", j, self.pts[i])
+        return nu
+
     def apply_K(self, y):
         """The common dense map of C1 X_r + C2 X_e given y (Eqs. def_c1_c2, definition_of_Q_matrix):
         out_i = sum_n w_n chi_i(x_i^n) Y(s_n) sum_j sum_l0m0 C_ik^j [P chi_j y_j]_l0m0 k^j_l0 Y^j_l0m0 (x_i^n).
         """
         mu = np.stack([self.lexpand(self.cik[j]) * (self._pchi(j) @ y[j]) for j in range(self.M)])
         out = np.zeros((self.M, self.nb))
+        if self.fmm_order > 0:
+            phi = self._potential(mu)
+            return np.stack([self.analysis(self.chi[i] * phi[i]) for i in range(self.M)])
         for i in range(self.M):
             phi = np.zeros(self.N)
             for j in range(self.M):
@@ -314,7 +358,9 @@ class DDLPB:
     def apply_KT(self, lam):
         """K^T lam (transpose of apply_K)."""
         nu = np.zeros((self.M, self.nb))
-        for i in range(self.M):
+        if self.fmm_order > 0:
+            nu = self._potential_T(np.stack([self.w * self.chi[i] * self.synthesis(lam[i]) for i in range(self.M)]))
+        for i in range(self.M if self.fmm_order == 0 else 0):
             zi = self.w * self.chi[i] * self.synthesis(lam[i])
             for j in range(self.M):
                 nu[j] += zi @ self.basis("k", j, self.pts[i])
@@ -385,7 +431,10 @@ class DDLPB:
         C0 = np.stack([self.analysis(self.chi[j] * self.dn_psi0(j)) for j in range(M)])
         mu0 = self.lexpand(self.cik) * C0
         F0 = np.zeros((M, self.nb))
-        for i in range(M):
+        if self.fmm_order > 0:
+            S_all = self._potential(mu0)
+            F0 = np.stack([-(self.eps1 / self.eps2) * self.analysis(self.chi[i] * S_all[i]) for i in range(M)])
+        for i in range(M if self.fmm_order == 0 else 0):
             S = np.zeros(self.N)
             for j in range(M):
                 S += self.basis("k", j, self.pts[i]) @ mu0[j]
@@ -404,7 +453,9 @@ class DDLPB:
         g = self.rhs()
         n = 2 * self.M * self.nb
         if dense is None:
-            dense = n <= 6000
+            dense = n <= 6000 and self.fmm_order == 0
+        if dense and self.fmm_order > 0:
+            raise ValueError("the dense assembly is direct; FMM mode solves matrix-free")
         if dense:
             self.L = self.assemble_L()
             X = np.linalg.solve(self.L, g.reshape(-1))
@@ -418,7 +469,9 @@ class DDLPB:
         Q = self.qvec()
         n = 2 * self.M * self.nb
         if dense is None:
-            dense = n <= 6000
+            dense = n <= 6000 and self.fmm_order == 0
+        if dense and self.fmm_order > 0:
+            raise ValueError("the dense assembly is direct; FMM mode solves matrix-free")
         if dense:
             if not hasattr(self, "L"):
                 self.L = self.assemble_L()
@@ -517,6 +570,8 @@ class DDLPB:
 
     def energy_gradient(self, X=None, Xa=None):
         """dE_s/dx_k = 1/2 <grad g - grad L X, X_adj> (Eq. force_lpb), all k at once."""
+        if self.fmm_order > 0:
+            raise NotImplementedError("forces differentiate the direct far field; not in FMM mode")
         X = self.X if X is None else X
         Xa = self.Xadj if Xa is None else Xa
         M = self.M
