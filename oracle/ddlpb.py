@@ -303,36 +303,52 @@ class DDLPB:
     # ---- FMM mode: the potential of the k-ratio multipoles at the points with chi > 0
     def _fmm(self):
         if self._tree is None:
-            from .fmm import YukawaTree
-            self._tree = YukawaTree(self.x, self.kappa, self.lmax, self.fmm_order)
+            from .fmm import YukawaFMM
+            self._tree = YukawaFMM(self.x, self.r, self.kappa, self.lmax, self.fmm_order)
             self._ext = [np.nonzero(self.chi[i] > 0)[0] for i in range(self.M)]
-            self._targets = np.concatenate([self.pts[i][self._ext[i]] for i in range(self.M)])
+            self._Yp = sph.ylm(self.fmm_order, self.s)                 # [N, (p+1)^2]
+            # near sources of each target sphere, and the near targets of each source sphere
+            self._near_t = [[] for _ in range(self.M)]
+            for i in range(self.M):
+                for j in self._tree.near[i]:
+                    self._near_t[j].append(i)
         return self._tree
 
     def _potential(self, mu):
         """phi[i, n] = sum_j k-ratio basis of j at x_i^n times mu_j, at the points with chi > 0
-        (zero elsewhere); by the tree when fmm_order > 0, else directly."""
+        (zero elsewhere in FMM mode); far field by the FMM when fmm_order > 0, else directly."""
         phi = np.zeros((self.M, self.N))
         if self.fmm_order > 0:
-            tree = self._fmm()
-            vals = tree.potential(mu / self.lexpand(self.k_r), self._targets)
-            o = 0
+            F = self._fmm()
+            Lc = F.locals(mu)
             for i in range(self.M):
-                k = len(self._ext[i])
-                phi[i, self._ext[i]] = vals[o:o + k]
-                o += k
+                e = self._ext[i]
+                if len(e) == 0:
+                    continue
+                phi[i, e] = self._Yp[e] @ Lc[i] + F.potential_direct(mu, self.pts[i][e], F.near[i])
             return phi
         for i in range(self.M):
             for j in range(self.M):
                 phi[i] += self.basis("k", j, self.pts[i]) @ mu[j]
         return phi
 
-    def _potential_T(self, z):
-        """Transpose of _potential for z[M, N] (only the entries with chi > 0 count)."""
+    def _potential_T(self, z, full=False):
+        """Transpose of _potential for z[M, N] (only the entries with chi > 0 count).  With full
+        (FMM mode), the far part is returned to degree fmm_order as a second array."""
         if self.fmm_order > 0:
-            tree = self._fmm()
-            zt = np.concatenate([z[i, self._ext[i]] for i in range(self.M)])
-            return tree.potential_T(zt, self._targets) / self.lexpand(self.k_r)
+            F = self._fmm()
+            lam = np.zeros((self.M, F.nbp))
+            for i in range(self.M):
+                e = self._ext[i]
+                lam[i] = z[i, e] @ self._Yp[e]
+            far = F.locals_T_full(lam)
+            nu = far[:, :self.nb].copy()
+            for j in range(self.M):
+                for i in self._near_t[j]:
+                    e = self._ext[i]
+                    if len(e):
+                        nu[j] += z[i, e] @ self.basis("k", j, self.pts[i][e])
+            return (nu, far) if full else nu
         nu = np.zeros((self.M, self.nb))
         for i in range(self.M):
             for j in range(self.M):
@@ -530,9 +546,13 @@ class DDLPB:
         phi = sum_j sum_l0m0 mu_j k^j Y^j, mu_j = C_ik^j sum_n0 w_n0 chi_j(x_j^n0) vsrc_j(n0) Y(s_n0),
         holding vsrc fixed: the derivative of chi_i (Eq. derivative_chi_i), of
         P chi_j / C0 (through chi_j), of k^j (Eq. Derivative_of_k_l0) and of Y^j
-        (Eq. derivative_ylm).  Returns the adjoint coefficients nu_j."""
+        (Eq. derivative_ylm).  Returns the adjoint coefficients nu_j.  In FMM mode the far
+        part of phi and of its gradient at the targets comes from the local expansions, and
+        the far part of the source-side gradient from the adjoint pass (Appendix)."""
         M = self.M
         mu = np.stack([self.lexpand(self.cik[j]) * self.analysis(self.chi[j] * vsrc[j]) for j in range(M)])
+        if self.fmm_order > 0:
+            return self._grad_K_fmm(G, mu, vsrc, zeta, scale)
         nu = np.zeros((M, self.nb))
         for i in range(M):
             phi = np.zeros(self.N)
@@ -554,12 +574,54 @@ class DDLPB:
             Gt = np.zeros_like(G)
             self._acc_dchi(Gt, i, zeta[i] * phi)
             G += scale * Gt
-        # source mask chi_j inside P chi_j / C0
-        for j in range(M):
+        self._acc_source_mask(G, vsrc, nu, scale)
+        return nu
+
+    def _acc_source_mask(self, G, vsrc, nu, scale):
+        """Source mask chi_j inside P chi_j / C0 (Eq. derivative_chi_i through Eq. definition_of_P_matrix)."""
+        for j in range(self.M):
             a = self.w * vsrc[j] * self.synthesis(self.lexpand(self.cik[j]) * nu[j])
             Gs = np.zeros_like(G)
             self._acc_dchi(Gs, j, a)
             G += scale * Gs
+
+    def _grad_K_fmm(self, G, mu, vsrc, zeta, scale):
+        from .fmm import basis_grad
+        F = self._fmm()
+        M, p = self.M, self.fmm_order
+        if p < self.lmax + 1:
+            raise ValueError("FMM-mode forces need fmm_order >= lmax + 1")
+        phi = self._potential(mu)
+        c = zeta * self.chi                                             # [M, N]
+        nu, far = self._potential_T(c, full=True)
+        Lc = F.locals(mu)
+        for i in range(M):
+            e = self._ext[i]
+            if len(e):
+                # target side: far field from the local expansion of sphere i, near sources directly
+                P = self.pts[i][e]
+                g = np.einsum("nbc,b->nc", basis_grad("R", p, self.kappa, P - self.x[i], self.r[i]), Lc[i])
+                for j in F.near[i]:
+                    if j != i:
+                        g += np.einsum("nbc,b->nc", self.basis("k", j, P, grad=True)[1], mu[j])
+                G[i] += scale * (c[i, e][:, None] * g).sum(0)
+            Gt = np.zeros_like(G)
+            self._acc_dchi(Gt, i, zeta[i] * phi[i])
+            G += scale * Gt
+        nd = (self.lmax + 2) ** 2
+        for j in range(M):
+            # source side: sum_t c_t grad (mu_j . k-basis_j)(x_t), far part through the gradient
+            # map of the degree lmax + 1 adjoint coefficients, near targets directly
+            D = F.gradient_map(j, self.lmax)                            # [3, nb, nd]
+            sg = np.einsum("anb,b,n->a", D, far[j, :nd], mu[j])
+            for i in self._near_t[j]:
+                e = self._ext[i]
+                if i == j or len(e) == 0:
+                    continue
+                dB = self.basis("k", j, self.pts[i][e], grad=True)[1]
+                sg += (c[i, e][:, None] * np.einsum("nbc,b->nc", dB, mu[j])).sum(0)
+            G[j] -= scale * sg
+        self._acc_source_mask(G, vsrc, nu, scale)
         return nu
 
     def hess_inv_r(self, d):
@@ -570,8 +632,6 @@ class DDLPB:
 
     def energy_gradient(self, X=None, Xa=None):
         """dE_s/dx_k = 1/2 <grad g - grad L X, X_adj> (Eq. force_lpb), all k at once."""
-        if self.fmm_order > 0:
-            raise NotImplementedError("forces differentiate the direct far field; not in FMM mode")
         X = self.X if X is None else X
         Xa = self.Xadj if Xa is None else Xa
         M = self.M
