@@ -64,10 +64,13 @@ typedef struct {
     double eta;          /* width of the smooth switch chi_eta (Eq. regular_char_function); default 0.1 */
     double tol;          /* relative residual ||g - L X|| / ||g|| of both solves; default 1e-8 */
     int max_iter;        /* cap on outer (FP64) Krylov iterations; default 500 */
-    int gmres_restart;   /* Krylov basis size before restart, 1..400; default 150 (the preconditioned
+    int gmres_restart;   /* Krylov basis size before restart, 1..2000; default 150 (the preconditioned
                             spectrum is real but spread, so short restarts stagnate) */
     int precision;       /* ddlpb_precision; default DDLPB_FP64 */
-    int fmm_order;       /* 0: direct summation of the dense coupling (the only mode of this build) */
+    int fmm_order;       /* 0: direct summation of the dense coupling; p in [lmax + 1, 22]: its far field
+                            by the fast multipole method of the Appendix with expansions of order p
+                            (binary tree over the Morton-ordered spheres, single-sphere leaves,
+                            near pairs summed directly); default 0 */
     void* cuda_stream;   /* cudaStream_t the context launches on; NULL = legacy default stream */
     double precond_tol;  /* relative tolerance of the inner A/B solves that apply the L_AB
                             preconditioner of Sec. 4 inside flexible GMRES; default 1e-3;
@@ -83,6 +86,8 @@ typedef struct {
                             preconditioner stream an FP16 copy of the stored A/B basis (FP32
                             arithmetic; an inexact preconditioner is allowed in flexible GMRES);
                             0: they use the FP32 basis; no effect in the FP64 form; default 1 */
+    double fmm_theta;    /* admissibility of the FMM: a target node A and source node B interact by
+                            M2L when Rt_A + Rs_B < fmm_theta |c_A - c_B|; in (0, 1); default 0.5 */
 } ddlpb_options;
 
 typedef struct {

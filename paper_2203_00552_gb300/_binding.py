@@ -29,7 +29,7 @@ class Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int), ("gmres_restart", C.c_int),
                 ("precision", C.c_int), ("fmm_order", C.c_int), ("cuda_stream", C.c_void_p),
                 ("precond_tol", C.c_double), ("kernel_timing", C.c_int), ("precond_coupling", C.c_int),
-                ("precond_fp16", C.c_int)]
+                ("precond_fp16", C.c_int), ("fmm_theta", C.c_double)]
 
 
 class Info(C.Structure):

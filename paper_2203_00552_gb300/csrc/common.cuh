@@ -15,7 +15,8 @@
 #include "ddlpb.h"
 
 #define DDLPB_LMAX_MAX 16
-#define DDLPB_LT (DDLPB_LMAX_MAX + 4)   // row stride of the (l, m) coefficient tables
+#define DDLPB_FMM_PMAX 22               // highest FMM expansion order (J of degree p in shared memory)
+#define DDLPB_LT 32                     // row stride of the (l, m) coefficient tables (degrees <= 31)
 #define DDLPB_TCHUNK 512                // hits per CTA of the transposed A/B product
 
 // ---------------------------------------------------------------------------
@@ -88,6 +89,67 @@ struct OpSet {
     float* Rc = nullptr;      // [L+1][8 G8]
     __half* Bh = nullptr;     // [nb][8 G8]   FP16 copy
     __half* Rh = nullptr;     // [L+1][8 G8]
+};
+
+// Tree and interaction lists of the Yukawa FMM (Appendix), built at setup when fmm_order > 0.
+// Nodes are numbered level by level (the root is 0; the children of a node are child0 and
+// child0 + 1); every leaf holds one sphere.  The M2L list is sorted by target node and cut into
+// chunks of at most DDLPB_FMM_CHUNK translations (work items whose partial sums are added per
+// target in a fixed order); a second view sorts it by source node for the transposed pass.
+#define DDLPB_FMM_CHUNK 16
+struct FmmTree {
+    bool on = false;
+    int p = 0, q = 0;                 // expansion order; degree of the leaf multipoles (min(p, lmax + 1))
+    double theta = 0.5;
+    int n_nodes = 0, depth = 0;
+    std::vector<int> lev;             // host: first node of each level, lev[depth + 1] = n_nodes
+    std::vector<int> host_child0;     // host copy of child0 (internal nodes per level)
+    int* order = nullptr;             // [M] spheres in Morton order
+    int* node_a = nullptr;            // [n_nodes] range of the sorted list
+    int* node_b = nullptr;
+    int* parent = nullptr;            // [n_nodes], -1 at the root
+    int* child0 = nullptr;            // [n_nodes], -1 at a leaf
+    int* leaf_sphere = nullptr;       // [n_nodes], -1 at an internal node
+    int* leaf_node = nullptr;         // [M]
+    double4* node_g = nullptr;        // [n_nodes] centre c, scale radius Rt
+    double* node_Rs = nullptr;        // [n_nodes] source radius
+    int n_m2l = 0;
+    int* m2l_t = nullptr;             // [n_m2l] target node (sorted)
+    int* m2l_s = nullptr;             // [n_m2l] source node
+    long long* m2l_off = nullptr;     // [n_m2l] coaxial block of the translation
+    int n_ck = 0;
+    int* ck_b = nullptr;              // [n_ck] chunk [ck_b, ck_e) of the target-sorted list
+    int* ck_e = nullptr;
+    int* tck_ptr = nullptr;           // [n_nodes + 1] chunks of target node k
+    int* m2lT_k = nullptr;            // [n_m2l] the list sorted by source node (indices into the above)
+    int n_ckT = 0;
+    int* ckT_b = nullptr;             // [n_ckT] chunk of the source-sorted view
+    int* ckT_e = nullptr;
+    int* sck_ptr = nullptr;           // [n_nodes + 1] chunks of source node k
+    long long* m2m_off = nullptr;     // [n_nodes] coaxial block of M2M(node -> parent)
+    long long* l2l_off = nullptr;     // [n_nodes] coaxial block of L2L(parent -> node)
+    long long* coax_off = nullptr;    // [n_m2l + 2 n_nodes] the three offset arrays above, contiguous
+    long long coax_size = 0;
+    int n_near = 0;
+    int* near_ptr = nullptr;          // [M + 1] near sources of target sphere i (leaf pairs, not admissible)
+    int* near_j = nullptr;
+    int* nearT_ptr = nullptr;         // [M + 1] near targets of source sphere j
+    int* nearT_i = nullptr;
+};
+
+// Per-precision data of the FMM: stored coaxial blocks, rotation table, Y_lm table to degree p
+// and the expansion buffers (translation vectors are always formed from the FP64 node centres).
+template <typename T>
+struct FmmOps {
+    using V4 = typename V4T<T>::type;
+    bool ready = false;
+    T* coax = nullptr;        // [coax_size] coaxial translation blocks
+    T* J = nullptr;           // rotation about x by -90 degrees, degree by degree
+    T* Yp = nullptr;          // [N][(p+1)^2] Y_lm(s_n), l <= p
+    T* Mx = nullptr;          // [n_nodes][(p+1)^2] multipoles (transposed pass: their adjoints)
+    T* Lx = nullptr;          // [n_nodes][(p+1)^2] locals (transposed pass: their adjoints)
+    T* part = nullptr;        // [max(n_ck, n_ckT)][(p+1)^2] partial sums of the chunks
+    T* leafq = nullptr;       // [M][(q+1)^2] adjoint of the leaf multipoles to degree q
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -181,6 +243,9 @@ struct ddlpb_ctx {
     double* tmpv = nullptr;     // [nvec]
     double* force_acc = nullptr;
     ForceScratch fscr;
+    FmmTree fmm;                // Yukawa FMM (fmm_order > 0)
+    FmmOps<double> fmm64;
+    FmmOps<float> fmm32;
     OpSet<double> d64;          // aliases the double tables above
     OpSet<float> f32;           // built on first use by the mixed-precision solve
     double centroid[3] = {0, 0, 0};
@@ -523,3 +588,8 @@ ddlpb_status solve_system(ddlpb_ctx* c, bool transpose, const double* b, double*
 ddlpb_status compute_forces(ddlpb_ctx* c, double* f_dev);
 void solver_state_free(ddlpb_ctx* c);
 ddlpb_status op_apply_fp32(ddlpb_ctx* c, int op, const double* x, double* y);
+// Yukawa FMM (fmm.cu): tree and lists at setup; potential of the sphere multipoles mu at the
+// external points (far field by the FMM, near pairs directly); its transpose.
+ddlpb_status fmm_build(ddlpb_ctx* c, const double* host_centres);
+template <typename T> ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext);
+template <typename T> ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu);

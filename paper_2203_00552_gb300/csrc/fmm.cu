@@ -1,0 +1,1209 @@
+// fmm.cu -- fast multipole method for the Yukawa far field of the coupling C (Appendix of
+// arXiv:2203.00552): the potential, at the external grid points, of the degree-lmax sphere
+// multipoles mu_j (k-ratio basis k_l(kappa|x - x_j|)/k_l(kappa r_j) Y_lm), and its transpose.
+//
+// Tree (built on the device at setup): spheres sorted by the Morton key of their centres; a
+// binary tree over the sorted list (node [a, b) splits at a + (b - a)/2) down to single-sphere
+// leaves.  Node centre c = midpoint of the bounding box of its centres; Rs = max |x_j - c|
+// (sources); Rt = max |x_j - c| + r_j (targets on the spheres), also the scale radius of the
+// node's expansions; a leaf has c = x_j, Rs = 0, Rt = r_j.  A dual traversal from (root, root)
+// emits an M2L for (target A, source B) when Rt_A + Rs_B < theta |c_A - c_B|, a near pair for
+// two leaves that fail the test, and otherwise splits A if B is a leaf or (A is not a leaf and
+// Rt_A >= Rs_B), else B.
+//
+// Expansions, order p: multipole sum M_lm k_l(kappa|x-c|)/k_l(kappa Rt) Y_lm, local
+// sum L_lm i_l(kappa|x-c|)/i_l(kappa Rt) Y_lm.  A leaf's multipole is mu_j (degree lmax; the
+// transposed pass returns it to degree q = lmax + 1 for the force gradients), and a leaf's
+// local evaluated on its own sphere is sum L_lm Y_lm(s_n).
+//
+// Translations (M2M, M2L, L2L, the Appendix's OZ-axis scheme): rotate the expansion so that the
+// translation vector is the z axis, translate along z (m is kept), rotate back.  Rotations use
+// the cheap rotation about z and a fixed table J (the rotation about x by -90 degrees, degree by
+// degree): a rotation about y by b is J Rz(b) J^T.  The coaxial coefficients come from the
+// addition theorem of the modified spherical Bessel functions (Gaunt integrals times i_b or k_b
+// of kappa t, b = l + a - 2j): for t = c_target - c_source along +z and input degree l, output a,
+//   M2L: (-1)^a     sum_j g k_b(kappa t)  i_a(kappa Rt_T) / k_l(kappa Rt_S)
+//   M2M: (-1)^(l+a) sum_j g i_b(kappa t)  k_a(kappa Rt_T) / k_l(kappa Rt_S)
+//   L2L:            sum_j g i_b(kappa t)  i_a(kappa Rt_T) / i_l(kappa Rt_S)
+// They are evaluated once per translation at setup in FP64 and stored in the precision of the
+// operator set (HBM holds them easily); the rotations are applied on the fly by one warp per
+// translation, with J in shared memory.
+//
+// Every pass gathers (one warp per target or per chunk of a target's list, partial sums added
+// in a fixed order), so the operator is deterministic: the mixed-precision refinement evaluates
+// it repeatedly and needs the same rounding each time.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "fmm_host.h"
+
+#define FMM_WARPS 4
+
+// ---------------------------------------------------------------- tree construction
+
+// Morton key of each centre: 21 bits per coordinate, floor(2^21 (x - lo) / side) clamped,
+// bits interleaved x, y, z from the most significant.
+__global__ void k_fmm_morton(int M, const double4* __restrict__ sph, double lx, double ly, double lz, double side,
+                             unsigned long long* __restrict__ key, int* __restrict__ idx) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const double4 s = sph[j];
+    const double lo[3] = {lx, ly, lz};
+    const double v[3] = {s.x, s.y, s.z};
+    unsigned long long q[3];
+    for (int d = 0; d < 3; ++d) {
+        double t = floor(__dmul_rn(__ddiv_rn(__dsub_rn(v[d], lo[d]), side), 2097152.0));
+        if (t > 2097151.0) t = 2097151.0;
+        if (t < 0.0) t = 0.0;
+        q[d] = (unsigned long long)t;
+    }
+    unsigned long long k = 0;
+    for (int b = 0; b < 21; ++b)
+        for (int d = 0; d < 3; ++d) k |= ((q[d] >> b) & 1ULL) << (3 * b + (2 - d));
+    key[j] = k;
+    idx[j] = j;
+}
+
+// Node geometry (FP64, written without fused multiply-adds so that the admissibility tests
+// round as the specification's plain arithmetic does).
+__global__ void k_fmm_node_geom(int n_nodes, const int* __restrict__ na, const int* __restrict__ nb,
+                                const int* __restrict__ order, const double4* __restrict__ sph,
+                                double4* __restrict__ g, double* __restrict__ Rs, int* __restrict__ leaf_sphere,
+                                int* __restrict__ leaf_node) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_nodes) return;
+    const int a = na[k], b = nb[k];
+    if (b - a == 1) {
+        const int j = order[a];
+        const double4 s = sph[j];
+        g[k] = s;
+        Rs[k] = 0.0;
+        leaf_sphere[k] = j;
+        leaf_node[j] = k;
+        return;
+    }
+    leaf_sphere[k] = -1;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int u = a; u < b; ++u) {
+        const double4 s = sph[order[u]];
+        lo[0] = fmin(lo[0], s.x); hi[0] = fmax(hi[0], s.x);
+        lo[1] = fmin(lo[1], s.y); hi[1] = fmax(hi[1], s.y);
+        lo[2] = fmin(lo[2], s.z); hi[2] = fmax(hi[2], s.z);
+    }
+    const double cx = __dmul_rn(0.5, __dadd_rn(lo[0], hi[0]));
+    const double cy = __dmul_rn(0.5, __dadd_rn(lo[1], hi[1]));
+    const double cz = __dmul_rn(0.5, __dadd_rn(lo[2], hi[2]));
+    double rs = 0.0, rt = 0.0;
+    for (int u = a; u < b; ++u) {
+        const double4 s = sph[order[u]];
+        const double dx = __dsub_rn(s.x, cx), dy = __dsub_rn(s.y, cy), dz = __dsub_rn(s.z, cz);
+        const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+        rs = fmax(rs, d);
+        rt = fmax(rt, __dadd_rn(d, s.w));
+    }
+    g[k] = make_double4(cx, cy, cz, rt);
+    Rs[k] = rs;
+}
+
+// One level of the dual traversal: every pair (A, B) of the frontier becomes an M2L, a near
+// pair, or two pairs of the next frontier.  Counters beyond a capacity are still counted (the
+// host then enlarges the arrays and traverses again); nothing is written past a capacity.
+__global__ void k_fmm_traverse(int n_front, const int2* __restrict__ front, const double4* __restrict__ g,
+                               const double* __restrict__ Rs, const int* __restrict__ child0, double theta,
+                               int2* __restrict__ next, int* __restrict__ n_next, int cap_next,
+                               int2* __restrict__ m2l, int* __restrict__ n_m2l, int cap_m2l,
+                               int2* __restrict__ near, int* __restrict__ n_near, int cap_near) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_front) return;
+    const int A = front[k].x, B = front[k].y;
+    const double4 ga = g[A], gb = g[B];
+    const double dx = __dsub_rn(ga.x, gb.x), dy = __dsub_rn(ga.y, gb.y), dz = __dsub_rn(ga.z, gb.z);
+    const double d = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    if (__dadd_rn(ga.w, Rs[B]) < __dmul_rn(theta, d)) {
+        const int u = atomicAdd(n_m2l, 1);
+        if (u < cap_m2l) m2l[u] = make_int2(A, B);
+        return;
+    }
+    const int ca = child0[A], cb = child0[B];
+    if (ca < 0 && cb < 0) {
+        const int u = atomicAdd(n_near, 1);
+        if (u < cap_near) near[u] = make_int2(A, B);
+        return;
+    }
+    const int u = atomicAdd(n_next, 2);
+    int2 p0, p1;
+    if (cb < 0 || (ca >= 0 && ga.w >= Rs[B])) {
+        p0 = make_int2(ca, B);
+        p1 = make_int2(ca + 1, B);
+    } else {
+        p0 = make_int2(A, cb);
+        p1 = make_int2(A, cb + 1);
+    }
+    if (u + 1 < cap_next) {
+        next[u] = p0;
+        next[u + 1] = p1;
+    }
+}
+
+// Segment starts of a sorted key array: ptr[k] = first position with key >= k, k = 0..K.
+__global__ void k_fmm_seg_starts(int n, int K, const int* __restrict__ keys, int* __restrict__ ptr) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u > n) return;
+    const int kp = u == 0 ? -1 : keys[u - 1];
+    const int kc = u == n ? K : keys[u];
+    for (int k = kp + 1; k <= kc; ++k) ptr[k] = u;
+}
+
+__global__ void k_fmm_split_pairs(int n, const int2* __restrict__ pr, int* __restrict__ a, int* __restrict__ b) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) {
+        a[u] = pr[u].x;
+        b[u] = pr[u].y;
+    }
+}
+
+// out[u] = k for the positions u of run k of a CSR (the key of every sorted entry).
+__global__ void k_fmm_fill_keys(int K, const int* __restrict__ ptr, int* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    for (int u = ptr[k]; u < ptr[k + 1]; ++u) out[u] = k;
+}
+
+__global__ void k_fmm_iota(int n, int* __restrict__ v) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) v[u] = u;
+}
+
+// Near pairs hold node ids; turn them into sphere ids.
+__global__ void k_fmm_near_spheres(int n, const int* __restrict__ leaf_sphere, int* __restrict__ a,
+                                   int* __restrict__ b) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) {
+        a[u] = leaf_sphere[a[u]];
+        b[u] = leaf_sphere[b[u]];
+    }
+}
+
+// Chunks of each node's run in a sorted list: count, then fill after the scan.
+__global__ void k_fmm_chunk_count(int K, const int* __restrict__ ptr, int* __restrict__ cnt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) cnt[k] = (ptr[k + 1] - ptr[k] + DDLPB_FMM_CHUNK - 1) / DDLPB_FMM_CHUNK;
+}
+
+__global__ void k_fmm_chunk_fill(int K, const int* __restrict__ ptr, const int* __restrict__ cpos,
+                                 int* __restrict__ cb, int* __restrict__ ce) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int c = cpos[k];
+    for (int u = ptr[k]; u < ptr[k + 1]; u += DDLPB_FMM_CHUNK, ++c) {
+        cb[c] = u;
+        ce[c] = min(u + DDLPB_FMM_CHUNK, ptr[k + 1]);
+    }
+}
+
+__device__ __forceinline__ long long coax_size_dev(int pin, int pout) {
+    long long s = 0;
+    for (int m = 0; m <= min(pin, pout); ++m) s += (long long)(pin + 1 - m) * (pout + 1 - m);
+    return s;
+}
+
+// Sizes of the coaxial blocks: the M2L list, then M2M(k -> parent) and L2L(parent -> k) per node.
+__global__ void k_fmm_coax_sizes(int n_m2l, int n_nodes, int p, int q, const int* __restrict__ m2l_s,
+                                 const int* __restrict__ child0, const int* __restrict__ parent,
+                                 long long* __restrict__ sz) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n_m2l) {
+        sz[u] = coax_size_dev(child0[m2l_s[u]] < 0 ? q : p, p);
+    } else if (u < n_m2l + n_nodes) {
+        const int k = u - n_m2l;
+        sz[u] = parent[k] < 0 ? 0 : coax_size_dev(child0[k] < 0 ? q : p, p);
+    } else if (u < n_m2l + 2 * n_nodes) {
+        const int k = u - n_m2l - n_nodes;
+        sz[u] = parent[k] < 0 ? 0 : coax_size_dev(p, p);
+    }
+}
+
+__global__ void k_fmm_coax_offsets(int n_m2l, int n_nodes, const long long* __restrict__ off,
+                                   long long* __restrict__ m2l_off, long long* __restrict__ m2m_off,
+                                   long long* __restrict__ l2l_off) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n_m2l) m2l_off[u] = off[u];
+    else if (u < n_m2l + n_nodes) m2m_off[u - n_m2l] = off[u];
+    else if (u < n_m2l + 2 * n_nodes) l2l_off[u - n_m2l - n_nodes] = off[u];
+}
+
+// k_n(x), n = 0..n_max (k_0 = exp(-x)/x; only ratios and products with i enter the blocks).
+__device__ void bessel_k_all(int n_max, double x, double* k) {
+    const double e = exp(-x);
+    k[0] = e / x;
+    if (n_max >= 1) k[1] = e * (1.0 + x) / (x * x);
+    for (int n = 1; n < n_max; ++n) k[n + 1] = k[n - 1] + (2.0 * n + 1.0) / x * k[n];
+}
+
+// i_n(x) = x^n S_n(x) / (2n+1)!!, n = 0..n_max (S_n the positive series, downward recurrence).
+__device__ void bessel_i_all(int n_max, double x, double* v) {
+    const double x2 = x * x;
+    double s1 = scaled_i_series<double>(n_max + 1, x), s0 = scaled_i_series<double>(n_max, x);
+    v[n_max] = s0;
+    for (int n = n_max - 1; n >= 0; --n) {
+        const double sn = s0 + x2 * s1 / (double)((2 * n + 3) * (2 * n + 5));
+        s1 = s0;
+        s0 = sn;
+        v[n] = sn;
+    }
+    double f = 1.0;
+    for (int n = 0; n <= n_max; ++n) {
+        v[n] *= f;
+        f *= x / (double)(2 * n + 3);
+    }
+}
+
+// The coaxial block of translation u (one CTA): kind 0 M2L, 1 M2M, 2 L2L.
+template <typename T>
+__global__ void k_fmm_coax(int n_m2l, int n_nodes, int p, int q, double kappa, const int* __restrict__ m2l_t,
+                           const int* __restrict__ m2l_s, const int* __restrict__ child0,
+                           const int* __restrict__ parent, const double4* __restrict__ g,
+                           const double* __restrict__ gtab, const long long* __restrict__ goff,
+                           const long long* __restrict__ off, T* __restrict__ coax) {
+    __shared__ double f[2 * DDLPB_FMM_PMAX + 2];
+    __shared__ double so[DDLPB_FMM_PMAX + 2], si[DDLPB_FMM_PMAX + 2];
+    const int u = blockIdx.x;
+    int kind, S, Tn;
+    if (u < n_m2l) {
+        kind = 0;
+        S = m2l_s[u];
+        Tn = m2l_t[u];
+    } else if (u < n_m2l + n_nodes) {
+        kind = 1;
+        S = u - n_m2l;
+        Tn = parent[S];
+    } else {
+        kind = 2;
+        Tn = u - n_m2l - n_nodes;
+        S = parent[Tn];
+    }
+    if (S < 0 || Tn < 0) return;   // the root has no M2M / L2L
+    const int pin = (kind != 2 && child0[S] < 0) ? q : p, pout = p;
+    const double4 gs = g[S], gt = g[Tn];
+    const double dx = gt.x - gs.x, dy = gt.y - gs.y, dz = gt.z - gs.z;
+    const double t = sqrt(dx * dx + dy * dy + dz * dz);
+    if (threadIdx.x == 0) {
+        double tmp[2 * DDLPB_FMM_PMAX + 2];
+        if (kind == 0) bessel_k_all(pin + pout, kappa * t, f);
+        else bessel_i_all(pin + pout, kappa * t, f);
+        // output scale (a <= pout) and input scale (l <= pin)
+        if (kind == 1) bessel_k_all(pout, kappa * gt.w, tmp);
+        else bessel_i_all(pout, kappa * gt.w, tmp);
+        for (int a = 0; a <= pout; ++a) so[a] = tmp[a];
+        if (kind == 2) bessel_i_all(pin, kappa * gs.w, tmp);
+        else bessel_k_all(pin, kappa * gs.w, tmp);
+        for (int l = 0; l <= pin; ++l) si[l] = 1.0 / tmp[l];
+    }
+    __syncthreads();
+    const long long base = off[u];
+    long long bo = 0;
+    for (int m = 0; m <= min(pin, pout); ++m) {
+        const int nl = pin + 1 - m, na = pout + 1 - m;
+        for (int e = threadIdx.x; e < nl * na; e += blockDim.x) {
+            const int l = m + e / na, a = m + e % na;
+            const double* gg = gtab + goff[((size_t)m * (p + 1) + l) * (p + 1) + a];
+            double s = 0.0;
+            for (int j = 0; j <= min(l, a); ++j) s += gg[j] * f[l + a - 2 * j];
+            double sign = 1.0;
+            if (kind == 0 && (a & 1)) sign = -1.0;
+            if (kind == 1 && ((l + a) & 1)) sign = -1.0;
+            coax[base + bo + e] = (T)(sign * s * so[a] * si[l]);
+        }
+        bo += (long long)nl * na;
+    }
+}
+
+// Y_lm(s_n) to degree p at the Lebedev points.
+template <typename T>
+__global__ void k_fmm_ytab(int N, int p, const double4* __restrict__ leb, YTab yt, T* __restrict__ Yp) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int nbp = (p + 1) * (p + 1);
+    const double4 s = leb[n];
+    ylm_stream<double>(p, s.x, s.y, s.z, yt, [&](int idx, int, double v) { Yp[(size_t)n * nbp + idx] = (T)v; });
+}
+
+// ---------------------------------------------------------------- warp translations
+
+__device__ __forceinline__ int deg_of(int idx) { return (int)sqrtf((float)idx + 0.5f); }
+
+// Per-warp scratch: two coefficient vectors and the angle tables cos/sin(m alpha), cos/sin(m beta).
+template <typename T>
+struct WarpScratch {
+    T* v;
+    T* w;
+    T* ca;
+    T* sa;
+    T* cb;
+    T* sb;
+};
+
+// Rotation about z of the coefficients of degree <= deg: Rz(s * angle) with the angle's
+// cos/sin(m angle) tables (s = +1 or -1).
+template <typename T>
+__device__ __forceinline__ void rot_z(T* v, int deg, const T* cm, const T* sm, T s, int lane) {
+    for (int idx = lane; idx < (deg + 1) * (deg + 1); idx += 32) {
+        const int l = deg_of(idx), m = idx - l * l - l;
+        if (m <= 0) continue;
+        const T c = cm[m], sn = s * sm[m];
+        const T a = v[idx], b = v[idx - 2 * m];
+        v[idx] = c * a - sn * b;
+        v[idx - 2 * m] = sn * a + c * b;
+    }
+    __syncwarp();
+}
+
+// out = J in (or J^T in), degree by degree, degree <= deg.
+template <typename T>
+__device__ __forceinline__ void rot_J(const T* __restrict__ J, const T* in, T* out, int deg, bool tr, int lane) {
+    for (int idx = lane; idx < (deg + 1) * (deg + 1); idx += 32) {
+        const int l = deg_of(idx), mi = idx - l * l, n = 2 * l + 1;
+        const T* Jl = J + (long long)l * (4LL * l * l - 1) / 3;
+        const T* x = in + l * l;
+        T s = 0;
+        if (tr) {
+            for (int mj = 0; mj < n; ++mj) s += Jl[mj * n + mi] * x[mj];
+        } else {
+            const T* row = Jl + mi * n;
+            for (int mj = 0; mj < n; ++mj) s += row[mj] * x[mj];
+        }
+        out[idx] = s;
+    }
+    __syncwarp();
+}
+
+// Coaxial step of a translation with forward degrees (pin -> pout): forward out = Z in (out
+// degree pout), transposed out = Z^T in (out degree pin).
+template <typename T>
+__device__ __forceinline__ void coax_apply(const T* __restrict__ Z, int pin, int pout, bool tr, const T* in, T* out,
+                                           int lane) {
+    const int dout = tr ? pin : pout;
+    for (int idx = lane; idx < (dout + 1) * (dout + 1); idx += 32) {
+        const int o = deg_of(idx), m = idx - o * o - o, am = m < 0 ? -m : m;
+        T s = 0;
+        if (am <= min(pin, pout)) {
+            long long bo = 0;
+            for (int mm = 0; mm < am; ++mm) bo += (long long)(pin + 1 - mm) * (pout + 1 - mm);
+            const int na = pout + 1 - am;
+            const T* blk = Z + bo;
+            if (!tr) {   // o = a: sum over input degrees l
+                for (int l = am; l <= pin; ++l) s += blk[(l - am) * na + (o - am)] * in[l * l + l + m];
+            } else {     // o = l: sum over output degrees a
+                const T* row = blk + (long long)(o - am) * na;
+                for (int a = am; a <= pout; ++a) s += row[a - am] * in[a * a + a + m];
+            }
+        }
+        out[idx] = s;
+    }
+    __syncwarp();
+}
+
+// Angle tables of the translation vector t (cos/sin of m alpha and m beta, m <= p).
+template <typename T>
+__device__ __forceinline__ void angles(T tx, T ty, T tz, int p, WarpScratch<T>& ws, int lane) {
+    const T rxy = sqrt(tx * tx + ty * ty);
+    const T alpha = rxy > (T)0 ? atan2(ty, tx) : (T)0;
+    const T beta = atan2(rxy, tz);
+    if (lane <= p) {
+        T s, c;
+        if constexpr (sizeof(T) == 8) {
+            sincos((double)lane * alpha, &s, &c);
+        } else {
+            sincosf((float)lane * alpha, &s, &c);
+        }
+        ws.ca[lane] = c;
+        ws.sa[lane] = s;
+        if constexpr (sizeof(T) == 8) {
+            sincos((double)lane * beta, &s, &c);
+        } else {
+            sincosf((float)lane * beta, &s, &c);
+        }
+        ws.cb[lane] = c;
+        ws.sb[lane] = s;
+    }
+    __syncwarp();
+}
+
+// One translation by the warp.  Forward: ws.v holds the input (degree pin), the result (degree
+// pout) is left in ws.w.  Transposed: ws.v holds degree pout, the result (degree pin) in ws.w.
+template <typename T>
+__device__ __forceinline__ void translate(const T* __restrict__ J, const T* __restrict__ Z, int pin, int pout,
+                                          bool tr, WarpScratch<T>& ws, int lane) {
+    const int d1 = tr ? pout : pin, d2 = tr ? pin : pout;
+    rot_z(ws.v, d1, ws.ca, ws.sa, (T)-1, lane);      // Rz(-alpha)
+    rot_J(J, ws.v, ws.w, d1, true, lane);            // J^T
+    rot_z(ws.w, d1, ws.cb, ws.sb, (T)-1, lane);      // Rz(-beta)
+    rot_J(J, ws.w, ws.v, d1, false, lane);           // J
+    coax_apply(Z, pin, pout, tr, ws.v, ws.w, lane);  // along z
+    rot_J(J, ws.w, ws.v, d2, true, lane);            // J^T
+    rot_z(ws.v, d2, ws.cb, ws.sb, (T)1, lane);       // Rz(beta)
+    rot_J(J, ws.v, ws.w, d2, false, lane);           // J
+    rot_z(ws.w, d2, ws.ca, ws.sa, (T)1, lane);       // Rz(alpha)
+}
+
+// Shared memory of a translation kernel: J, then per warp v, w (nbp each), acc (nbp), 4 (p+1) angles.
+template <typename T>
+__device__ __forceinline__ WarpScratch<T> warp_scratch(T* sm, long long jsize, int nbp, int warp, T** acc) {
+    T* base = sm + jsize + (long long)warp * (3 * nbp + 4 * 32);
+    WarpScratch<T> ws;
+    ws.v = base;
+    ws.w = base + nbp;
+    *acc = base + 2 * nbp;
+    ws.ca = base + 3 * nbp;
+    ws.sa = ws.ca + 32;
+    ws.cb = ws.sa + 32;
+    ws.sb = ws.cb + 32;
+    return ws;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_J(T* sm, const T* __restrict__ J, long long jsize) {
+    for (long long k = threadIdx.x; k < jsize; k += blockDim.x) sm[k] = J[k];
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- forward pass
+
+// Leaf multipoles: the sphere multipoles mu_j (degree lmax), zero above.
+template <typename T>
+__global__ void k_fmm_leaf_mult(int M, int nb, int nbp, const int* __restrict__ leaf_node, const T* __restrict__ mu,
+                                T* __restrict__ Mx) {
+    const int j = blockIdx.x;
+    T* out = Mx + (size_t)leaf_node[j] * nbp;
+    for (int k = threadIdx.x; k < nbp; k += blockDim.x) out[k] = k < nb ? mu[(size_t)j * nb + k] : (T)0;
+}
+
+// M2M into the internal nodes [first, first + count) of one level: M_P = sum_c M2M(c -> P) M_c.
+template <typename T, typename V4>
+__global__ void k_fmm_m2m(int first, int count, int p, int q, long long jsize, const int* __restrict__ child0,
+                          const long long* __restrict__ m2m_off, const double4* __restrict__ nc, const T* __restrict__ J,
+                          const T* __restrict__ coax, T* __restrict__ Mx) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int k = first + blockIdx.x * FMM_WARPS + warp;
+    if (k >= first + count) return;
+    const int c0 = child0[k];
+    if (c0 < 0) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    const double4 P = nc[k];
+    for (int c = c0; c <= c0 + 1; ++c) {
+        const int pin = child0[c] < 0 ? q : p;
+        const double4 C = nc[c];
+        angles<T>((T)(P.x - C.x), (T)(P.y - C.y), (T)(P.z - C.z), p, ws, lane);
+        const T* src = Mx + (size_t)c * nbp;
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = i < (pin + 1) * (pin + 1) ? src[i] : (T)0;
+        __syncwarp();
+        translate(sm, coax + m2m_off[c], pin, p, false, ws, lane);
+        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < nbp; i += 32) Mx[(size_t)k * nbp + i] = acc[i];
+}
+
+// M2L, one warp per chunk of the target-sorted list; the chunk's sum goes to part[chunk].
+template <typename T, typename V4>
+__global__ void k_fmm_m2l(int n_ck, int p, int q, long long jsize, const int* __restrict__ ck_b,
+                          const int* __restrict__ ck_e, const int* __restrict__ m2l_t, const int* __restrict__ m2l_s,
+                          const long long* __restrict__ m2l_off, const int* __restrict__ child0,
+                          const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
+                          const T* __restrict__ Mx, T* __restrict__ part) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int ck = blockIdx.x * FMM_WARPS + warp;
+    if (ck >= n_ck) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    for (int u = ck_b[ck]; u < ck_e[ck]; ++u) {
+        const int A = m2l_t[u], B = m2l_s[u];
+        const int pin = child0[B] < 0 ? q : p;
+        const double4 ca = nc[A], cb = nc[B];
+        angles<T>((T)(ca.x - cb.x), (T)(ca.y - cb.y), (T)(ca.z - cb.z), p, ws, lane);
+        const T* src = Mx + (size_t)B * nbp;
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = i < (pin + 1) * (pin + 1) ? src[i] : (T)0;
+        __syncwarp();
+        translate(sm, coax + m2l_off[u], pin, p, false, ws, lane);
+        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < nbp; i += 32) part[(size_t)ck * nbp + i] = acc[i];
+}
+
+// Locals of the nodes [first, first + count) of one level: L_C = sum of C's M2L chunks +
+// L2L(parent -> C) L_parent.
+template <typename T, typename V4>
+__global__ void k_fmm_l2l(int first, int count, int p, long long jsize, const int* __restrict__ parent,
+                          const int* __restrict__ tck_ptr, const T* __restrict__ part,
+                          const long long* __restrict__ l2l_off, const double4* __restrict__ nc, const T* __restrict__ J,
+                          const T* __restrict__ coax, T* __restrict__ Lx) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int k = first + blockIdx.x * FMM_WARPS + warp;
+    if (k >= first + count) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    for (int ck = tck_ptr[k]; ck < tck_ptr[k + 1]; ++ck)
+        for (int i = lane; i < nbp; i += 32) acc[i] += part[(size_t)ck * nbp + i];
+    const int P = parent[k];
+    if (P >= 0) {
+        const double4 cc = nc[k], cp = nc[P];
+        angles<T>((T)(cc.x - cp.x), (T)(cc.y - cp.y), (T)(cc.z - cp.z), p, ws, lane);
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)P * nbp + i];
+        __syncwarp();
+        translate(sm, coax + l2l_off[k], p, p, false, ws, lane);
+        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
+    }
+    __syncwarp();
+    for (int i = lane; i < nbp; i += 32) Lx[(size_t)k * nbp + i] = acc[i];
+}
+
+// Potential at the external points of target sphere i: the leaf local (sum L_lm Y_lm(s_n)) plus
+// the near sources summed directly.  Offsets to the near sources are formed in FP64 and then
+// rounded, so the FP32 set keeps full relative accuracy near the sources.
+template <typename T, typename V4>
+__global__ void k_fmm_leaf_pot(int N, int nb, int L, int p, T kappa, const int* __restrict__ ext_ptr,
+                               const int* __restrict__ ext_p, const double4* __restrict__ sph64,
+                               const double4* __restrict__ leb64, const int* __restrict__ leaf_node,
+                               const T* __restrict__ Lx, const T* __restrict__ Yp, const int* __restrict__ near_ptr,
+                               const int* __restrict__ near_j, const T* __restrict__ mu, const T* __restrict__ Khinv,
+                               YTabT<T> yt, T* __restrict__ phi) {
+    extern __shared__ unsigned char smraw[];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    const int nbp = (p + 1) * (p + 1);
+    T* Li = (T*)smraw;
+    T* rad = Li + nbp;
+    const int i = blockIdx.x;
+    const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+    if (cnt == 0) return;
+    for (int k = tid; k < nbp; k += bd) Li[k] = Lx[(size_t)leaf_node[i] * nbp + k];
+    __syncthreads();
+    const double4 a = sph64[i];
+    const int k0 = near_ptr[i], k1 = near_ptr[i + 1];
+    for (int t = t0 + tid; t < t0 + cnt; t += bd) {
+        const int n = ext_p[t] % N;
+        const T* Y = Yp + (size_t)n * nbp;
+        T acc = 0;
+        for (int k = 0; k < nbp; ++k) acc += Li[k] * __ldg(Y + k);
+        const double4 s = leb64[n];
+        for (int kk = k0; kk < k1; ++kk) {
+            const int j = near_j[kk];
+            const double4 b = sph64[j];
+            const T dx = (T)(a.x - b.x + a.w * s.x), dy = (T)(a.y - b.y + a.w * s.y), dz = (T)(a.z - b.z + a.w * s.z);
+            const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(2, L, rho, (T)b.w, kappa, Khinv + (size_t)j * (L + 2), rad + tid, nullptr, bd);
+            const T* m = mu + (size_t)j * nb;
+            T v = 0;
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
+                          [&](int idx, int l, T yv) { v += __ldg(m + idx) * rad[tid + l * bd] * yv; });
+            acc += v;
+        }
+        phi[t] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- transposed pass
+
+// Adjoint of the leaf locals: Lambda_i = sum_t c_t Y_lm(s_n) over the external points of i.
+template <typename T>
+__global__ void k_fmm_leaf_lambda(int N, int p, const int* __restrict__ ext_ptr, const int* __restrict__ ext_p,
+                                  const int* __restrict__ leaf_node, const T* __restrict__ Yp,
+                                  const T* __restrict__ cext, T* __restrict__ Lx) {
+    extern __shared__ unsigned char smraw[];
+    const int i = blockIdx.x;
+    const int nbp = (p + 1) * (p + 1);
+    const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+    T* cv = (T*)smraw;
+    int* nn = (int*)(cv + N);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        cv[k] = cext[t0 + k];
+        nn[k] = ext_p[t0 + k] % N;
+    }
+    __syncthreads();
+    T* out = Lx + (size_t)leaf_node[i] * nbp;
+    for (int idx = threadIdx.x; idx < nbp; idx += blockDim.x) {
+        T s = 0;
+        for (int k = 0; k < cnt; ++k) s += cv[k] * Yp[(size_t)nn[k] * nbp + idx];
+        out[idx] = s;
+    }
+}
+
+// Transposed L2L, one level: Lambda_P = sum_c L2L(P -> c)^T Lambda_c for the internal nodes.
+template <typename T, typename V4>
+__global__ void k_fmm_l2l_T(int first, int count, int p, long long jsize, const int* __restrict__ child0,
+                            const long long* __restrict__ l2l_off, const double4* __restrict__ nc,
+                            const T* __restrict__ J, const T* __restrict__ coax, T* __restrict__ Lx) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int k = first + blockIdx.x * FMM_WARPS + warp;
+    if (k >= first + count) return;
+    const int c0 = child0[k];
+    if (c0 < 0) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    const double4 P = nc[k];
+    for (int c = c0; c <= c0 + 1; ++c) {
+        const double4 C = nc[c];
+        angles<T>((T)(C.x - P.x), (T)(C.y - P.y), (T)(C.z - P.z), p, ws, lane);
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)c * nbp + i];
+        __syncwarp();
+        translate(sm, coax + l2l_off[c], p, p, true, ws, lane);
+        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < nbp; i += 32) Lx[(size_t)k * nbp + i] = acc[i];
+}
+
+// Transposed M2L, one warp per chunk of the source-sorted view: part[chunk] = sum of
+// M2L(B -> A)^T Lambda_A over the chunk (degree of B's multipole).
+template <typename T, typename V4>
+__global__ void k_fmm_m2l_T(int n_ck, int p, int q, long long jsize, const int* __restrict__ ck_b,
+                            const int* __restrict__ ck_e, const int* __restrict__ m2lT_k,
+                            const int* __restrict__ m2l_t, const int* __restrict__ m2l_s,
+                            const long long* __restrict__ m2l_off, const int* __restrict__ child0,
+                            const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
+                            const T* __restrict__ Lx, T* __restrict__ part) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int ck = blockIdx.x * FMM_WARPS + warp;
+    if (ck >= n_ck) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    for (int v = ck_b[ck]; v < ck_e[ck]; ++v) {
+        const int u = m2lT_k[v];
+        const int A = m2l_t[u], B = m2l_s[u];
+        const int pin = child0[B] < 0 ? q : p;
+        const double4 ca = nc[A], cb = nc[B];
+        angles<T>((T)(ca.x - cb.x), (T)(ca.y - cb.y), (T)(ca.z - cb.z), p, ws, lane);
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)A * nbp + i];
+        __syncwarp();
+        translate(sm, coax + m2l_off[u], pin, p, true, ws, lane);
+        for (int i = lane; i < (pin + 1) * (pin + 1); i += 32) acc[i] += ws.w[i];
+        __syncwarp();
+    }
+    for (int i = lane; i < nbp; i += 32) part[(size_t)ck * nbp + i] = acc[i];
+}
+
+// Adjoint multipoles of the nodes [first, first + count) of one level: Psi_C = sum of C's
+// transposed M2L chunks + M2M(C -> parent)^T Psi_parent.
+template <typename T, typename V4>
+__global__ void k_fmm_m2m_T(int first, int count, int p, int q, long long jsize, const int* __restrict__ parent,
+                            const int* __restrict__ child0, const int* __restrict__ sck_ptr,
+                            const T* __restrict__ part, const long long* __restrict__ m2m_off,
+                            const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
+                            T* __restrict__ Mx) {
+    extern __shared__ unsigned char smraw[];
+    T* sm = (T*)smraw;
+    load_J(sm, J, jsize);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nbp = (p + 1) * (p + 1);
+    const int k = first + blockIdx.x * FMM_WARPS + warp;
+    if (k >= first + count) return;
+    T* acc;
+    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
+    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
+    for (int ck = sck_ptr[k]; ck < sck_ptr[k + 1]; ++ck)
+        for (int i = lane; i < nbp; i += 32) acc[i] += part[(size_t)ck * nbp + i];
+    const int P = parent[k];
+    if (P >= 0) {
+        const int pin = child0[k] < 0 ? q : p;
+        const double4 cc = nc[k], cp = nc[P];
+        angles<T>((T)(cp.x - cc.x), (T)(cp.y - cc.y), (T)(cp.z - cc.z), p, ws, lane);
+        for (int i = lane; i < nbp; i += 32) ws.v[i] = Mx[(size_t)P * nbp + i];
+        __syncwarp();
+        translate(sm, coax + m2m_off[k], pin, p, true, ws, lane);
+        for (int i = lane; i < (pin + 1) * (pin + 1); i += 32) acc[i] += ws.w[i];
+    }
+    __syncwarp();
+    for (int i = lane; i < nbp; i += 32) Mx[(size_t)k * nbp + i] = acc[i];
+}
+
+// nu_j = (far adjoint of the leaf multipole, l <= lmax) + sum over the near targets t of
+// sphere j's near list of c_t k-ratio basis of j at x_t.  Also keeps the far part to degree q.
+// Spheres without external points are no sources of the coupling (P chi_j = 0): their rows of
+// nu are left untouched (zero), since the forward pass reads every sphere's multipole.
+template <typename T, typename V4>
+__global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, const int* __restrict__ ext_ptr,
+                               const int* __restrict__ ext_p, const double4* __restrict__ sph64,
+                               const double4* __restrict__ leb64, const int* __restrict__ leaf_node,
+                               const T* __restrict__ Mx, const int* __restrict__ nearT_ptr,
+                               const int* __restrict__ nearT_i, const T* __restrict__ cext,
+                               const T* __restrict__ Khinv, YTabT<T> yt, T* __restrict__ nu, T* __restrict__ leafq) {
+    extern __shared__ unsigned char smraw[];
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+    const int nbp = (p + 1) * (p + 1), nq = (q + 1) * (q + 1);
+    T* acc = (T*)smraw;
+    T* kh = acc + nw * nb;
+    T* rad = kh + (L + 2);
+    const int j = blockIdx.x;
+    if (ext_ptr[j + 1] == ext_ptr[j]) return;
+    const double4 b = sph64[j];
+    for (int k = tid; k < nw * nb; k += bd) acc[k] = 0;
+    for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
+    __syncthreads();
+    for (int kk = nearT_ptr[j]; kk < nearT_ptr[j + 1]; ++kk) {
+        const int i = nearT_i[kk];
+        const double4 a = sph64[i];
+        const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+        for (int base = 0; base < cnt; base += bd) {
+            T dx = (T)b.w, dy = 0, dz = 0, c = 0;
+            if (base + tid < cnt) {
+                const int t = t0 + base + tid;
+                const double4 s = leb64[ext_p[t] % N];
+                dx = (T)(a.x - b.x + a.w * s.x);
+                dy = (T)(a.y - b.y + a.w * s.y);
+                dz = (T)(a.z - b.z + a.w * s.z);
+                c = cext[t];
+            }
+            const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+            radial<T>(2, L, rho, (T)b.w, kappa, kh, rad + tid, nullptr, bd);
+            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt, [&](int idx, int l, T yv) {
+                const T v = warp_sum(c * rad[tid + l * bd] * yv);
+                if (lane == 0) acc[warp * nb + idx] += v;
+            });
+        }
+    }
+    __syncthreads();
+    const T* far = Mx + (size_t)leaf_node[j] * nbp;
+    for (int idx = tid; idx < nb; idx += bd) {
+        T s = far[idx];
+        for (int w = 0; w < nw; ++w) s += acc[w * nb + idx];
+        nu[(size_t)j * nb + idx] = s;
+    }
+    if (leafq)
+        for (int idx = tid; idx < nq; idx += bd) leafq[(size_t)j * nq + idx] = far[idx];
+}
+
+// ---------------------------------------------------------------- host
+
+static ddlpb_status fmm_scan_ll(ddlpb_ctx* c, const long long* in, long long* out, int n) {
+    size_t bytes = 0;
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, c->stream));
+    void* tmp = nullptr;
+    DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, n, c->stream));
+    return DDLPB_OK;
+}
+
+static ddlpb_status fmm_scan_int(ddlpb_ctx* c, const int* in, int* out, int n) {
+    size_t bytes = 0;
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, c->stream));
+    void* tmp = nullptr;
+    DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+    DDLPB_CK(c, cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, n, c->stream));
+    return DDLPB_OK;
+}
+
+template <typename TK, typename TV>
+static ddlpb_status fmm_sort_pairs(ddlpb_ctx* c, const TK* kin, TK* kout, const TV* vin, TV* vout, int n, int bits) {
+    if (n <= 0) return DDLPB_OK;
+    size_t bytes = 0;
+    DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(nullptr, bytes, kin, kout, vin, vout, n, 0, bits, c->stream));
+    void* tmp = nullptr;
+    DDLPB_TRY(ctx_alloc(c, (char**)&tmp, bytes));
+    DDLPB_CK(c, cub::DeviceRadixSort::SortPairs(tmp, bytes, kin, kout, vin, vout, n, 0, bits, c->stream));
+    return DDLPB_OK;
+}
+
+static int bits_for(int n) {
+    int b = 1;
+    while ((1LL << b) < (long long)n + 1) ++b;
+    return b;
+}
+
+// Sorted (key, value) pairs -> CSR over K keys and the values in key order.
+static ddlpb_status fmm_csr(ddlpb_ctx* c, const int* keys, const int* vals, int n, int K, int** ptr, int** vout) {
+    int *ks = nullptr;
+    DDLPB_TRY(ctx_alloc(c, &ks, std::max(n, 1)));
+    DDLPB_TRY(ctx_alloc(c, vout, std::max(n, 1)));
+    DDLPB_TRY(ctx_alloc(c, ptr, K + 1));
+    DDLPB_TRY(fmm_sort_pairs(c, keys, ks, vals, *vout, n, bits_for(K)));
+    k_fmm_seg_starts<<<ceil_div(n + 1, 256), 256, 0, c->stream>>>(n, K, ks, *ptr);
+    DDLPB_LAUNCHED(c, "fmm_seg_starts");
+    return DDLPB_OK;
+}
+
+// Chunks of at most DDLPB_FMM_CHUNK entries of each of K runs given by ptr.
+static ddlpb_status fmm_chunks(ddlpb_ctx* c, const int* ptr, int K, int* n_ck, int** cb, int** ce, int** ckptr) {
+    int* cnt = nullptr;
+    DDLPB_TRY(ctx_alloc(c, &cnt, K + 1));
+    DDLPB_TRY(ctx_alloc(c, ckptr, K + 1));
+    DDLPB_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int) * (K + 1), c->stream));
+    k_fmm_chunk_count<<<ceil_div(K, 256), 256, 0, c->stream>>>(K, ptr, cnt);
+    DDLPB_LAUNCHED(c, "fmm_chunk_count");
+    DDLPB_TRY(fmm_scan_int(c, cnt, *ckptr, K + 1));
+    int n = 0;
+    DDLPB_CK(c, cudaMemcpyAsync(&n, *ckptr + K, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    DDLPB_CK(c, cudaStreamSynchronize(c->stream));
+    *n_ck = n;
+    DDLPB_TRY(ctx_alloc(c, cb, std::max(n, 1)));
+    DDLPB_TRY(ctx_alloc(c, ce, std::max(n, 1)));
+    k_fmm_chunk_fill<<<ceil_div(K, 256), 256, 0, c->stream>>>(K, ptr, *ckptr, *cb, *ce);
+    DDLPB_LAUNCHED(c, "fmm_chunk_fill");
+    return DDLPB_OK;
+}
+
+ddlpb_status fmm_build(ddlpb_ctx* c, const double* hc) {
+    FmmTree& F = c->fmm;
+    const int M = c->M, p = c->opt.fmm_order;
+    cudaStream_t st = c->stream;
+    F.on = true;
+    F.p = p;
+    F.q = std::min(p, c->lmax + 1);
+    F.theta = c->opt.fmm_theta;
+    // -- topology: ranges of the sorted list, level by level (depends on M only)
+    std::vector<int> na(1, 0), nbv(1, M), par(1, -1);
+    F.lev.assign(1, 0);
+    for (size_t lo = 0; lo < na.size();) {
+        const size_t hi = na.size();
+        for (size_t k = lo; k < hi; ++k) {
+            const int a = na[k], b = nbv[k];
+            if (b - a >= 2) {
+                const int m = a + (b - a) / 2;
+                na.push_back(a); nbv.push_back(m); par.push_back((int)k);
+                na.push_back(m); nbv.push_back(b); par.push_back((int)k);
+            }
+        }
+        if (na.size() > hi) F.lev.push_back((int)hi);
+        lo = hi;
+    }
+    const int n_nodes = (int)na.size();
+    F.lev.push_back(n_nodes);
+    std::vector<int> ch0(n_nodes, -1);
+    for (int k = 1; k < n_nodes; ++k)
+        if (ch0[par[k]] < 0) ch0[par[k]] = k;
+    F.n_nodes = n_nodes;
+    F.depth = (int)F.lev.size() - 2;
+    F.host_child0 = ch0;
+    DDLPB_TRY(ctx_alloc(c, &F.node_a, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.node_b, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.parent, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.child0, n_nodes));
+    DDLPB_CK(c, cudaMemcpyAsync(F.node_a, na.data(), sizeof(int) * n_nodes, cudaMemcpyHostToDevice, st));
+    DDLPB_CK(c, cudaMemcpyAsync(F.node_b, nbv.data(), sizeof(int) * n_nodes, cudaMemcpyHostToDevice, st));
+    DDLPB_CK(c, cudaMemcpyAsync(F.parent, par.data(), sizeof(int) * n_nodes, cudaMemcpyHostToDevice, st));
+    DDLPB_CK(c, cudaMemcpyAsync(F.child0, ch0.data(), sizeof(int) * n_nodes, cudaMemcpyHostToDevice, st));
+    // -- Morton order of the centres
+    double lx = hc[0], ly = hc[1], lz = hc[2], hx = hc[0], hy = hc[1], hz = hc[2];
+    for (int k = 1; k < M; ++k) {
+        lx = std::min(lx, hc[3 * k]); hx = std::max(hx, hc[3 * k]);
+        ly = std::min(ly, hc[3 * k + 1]); hy = std::max(hy, hc[3 * k + 1]);
+        lz = std::min(lz, hc[3 * k + 2]); hz = std::max(hz, hc[3 * k + 2]);
+    }
+    double side = std::max(hx - lx, std::max(hy - ly, hz - lz));
+    if (!(side > 0.0)) side = 1.0;
+    {
+        unsigned long long *kin = nullptr, *kout = nullptr;
+        int* vin = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &kin, M));
+        DDLPB_TRY(ctx_alloc(c, &kout, M));
+        DDLPB_TRY(ctx_alloc(c, &vin, M));
+        DDLPB_TRY(ctx_alloc(c, &F.order, M));
+        k_fmm_morton<<<ceil_div(M, 256), 256, 0, st>>>(M, c->sph, lx, ly, lz, side, kin, vin);
+        DDLPB_LAUNCHED(c, "fmm_morton");
+        DDLPB_TRY(fmm_sort_pairs(c, kin, kout, vin, F.order, M, 63));
+    }
+    // -- node geometry
+    DDLPB_TRY(ctx_alloc(c, &F.node_g, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.node_Rs, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.leaf_sphere, n_nodes));
+    DDLPB_TRY(ctx_alloc(c, &F.leaf_node, M));
+    k_fmm_node_geom<<<ceil_div(n_nodes, 128), 128, 0, st>>>(n_nodes, F.node_a, F.node_b, F.order, c->sph, F.node_g,
+                                                             F.node_Rs, F.leaf_sphere, F.leaf_node);
+    DDLPB_LAUNCHED(c, "fmm_node_geom");
+    // -- dual traversal, level by level (retried with larger arrays if a capacity was exceeded)
+    long long cap_front = 64LL * n_nodes + 1024, cap_m2l = 256LL * n_nodes + 1024, cap_near = 64LL * M + 1024;
+    int2 *m2l = nullptr, *near = nullptr;
+    int n_m2l = 0, n_near = 0;
+    for (int attempt = 0;; ++attempt) {
+        int2 *fa = nullptr, *fb = nullptr;
+        int* cnt = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &fa, cap_front));
+        DDLPB_TRY(ctx_alloc(c, &fb, cap_front));
+        DDLPB_TRY(ctx_alloc(c, &m2l, cap_m2l));
+        DDLPB_TRY(ctx_alloc(c, &near, cap_near));
+        DDLPB_TRY(ctx_alloc(c, &cnt, 3));
+        const int2 root = make_int2(0, 0);
+        DDLPB_CK(c, cudaMemcpyAsync(fa, &root, sizeof(int2), cudaMemcpyHostToDevice, st));
+        DDLPB_CK(c, cudaMemsetAsync(cnt, 0, 3 * sizeof(int), st));
+        int n_front = 1, h[3] = {0, 0, 0};
+        bool overflow = false;
+        long long max_front = 1;
+        for (int level = 0; n_front > 0 && level < 4 * (F.depth + 2); ++level) {
+            DDLPB_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), st));
+            k_fmm_traverse<<<ceil_div(n_front, 256), 256, 0, st>>>(n_front, fa, F.node_g, F.node_Rs, F.child0, F.theta,
+                                                                   fb, cnt, (int)cap_front, m2l, cnt + 1, (int)cap_m2l,
+                                                                   near, cnt + 2, (int)cap_near);
+            DDLPB_LAUNCHED(c, "fmm_traverse");
+            DDLPB_CK(c, cudaMemcpyAsync(h, cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            DDLPB_CK(c, cudaStreamSynchronize(st));
+            if (h[0] > cap_front || h[1] > cap_m2l || h[2] > cap_near) {
+                overflow = true;
+                max_front = std::max<long long>(max_front, h[0]);
+                break;
+            }
+            n_front = h[0];
+            std::swap(fa, fb);
+        }
+        if (!overflow && n_front > 0) {
+            c->err = "FMM traversal did not terminate";
+            return DDLPB_ECUDA;
+        }
+        if (!overflow) {
+            n_m2l = h[1];
+            n_near = h[2];
+            break;
+        }
+        if (attempt >= 3) {
+            c->err = "FMM interaction lists exceed their capacity";
+            return DDLPB_ENOMEM;
+        }
+        cap_front = std::max(cap_front * 4, max_front + 1024);
+        cap_m2l *= 4;
+        cap_near *= 4;
+    }
+    F.n_m2l = n_m2l;
+    F.n_near = n_near;
+    // -- M2L list sorted by target, chunks; the source-sorted view
+    {
+        int *t = nullptr, *s = nullptr, *tptr = nullptr, *sorted_s = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &t, std::max(n_m2l, 1)));
+        DDLPB_TRY(ctx_alloc(c, &s, std::max(n_m2l, 1)));
+        if (n_m2l > 0) {
+            k_fmm_split_pairs<<<ceil_div(n_m2l, 256), 256, 0, st>>>(n_m2l, m2l, t, s);
+            DDLPB_LAUNCHED(c, "fmm_split_pairs");
+        }
+        DDLPB_TRY(fmm_csr(c, t, s, n_m2l, n_nodes, &tptr, &sorted_s));
+        F.m2l_s = sorted_s;
+        DDLPB_TRY(ctx_alloc(c, &F.m2l_t, std::max(n_m2l, 1)));
+        k_fmm_fill_keys<<<ceil_div(n_nodes, 256), 256, 0, st>>>(n_nodes, tptr, F.m2l_t);
+        DDLPB_LAUNCHED(c, "fmm_fill_keys");
+        DDLPB_TRY(fmm_chunks(c, tptr, n_nodes, &F.n_ck, &F.ck_b, &F.ck_e, &F.tck_ptr));
+        // by source: keys m2l_s (sorted list order), values = position in the sorted list
+        int* pos = nullptr;
+        int* sptr = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &pos, std::max(n_m2l, 1)));
+        if (n_m2l > 0) {
+            k_fmm_iota<<<ceil_div(n_m2l, 256), 256, 0, st>>>(n_m2l, pos);
+            DDLPB_LAUNCHED(c, "fmm_iota");
+        }
+        DDLPB_TRY(fmm_csr(c, F.m2l_s, pos, n_m2l, n_nodes, &sptr, &F.m2lT_k));
+        DDLPB_TRY(fmm_chunks(c, sptr, n_nodes, &F.n_ckT, &F.ckT_b, &F.ckT_e, &F.sck_ptr));
+    }
+    // -- near pairs (node ids -> sphere ids), CSR by target and by source sphere
+    {
+        int *a = nullptr, *b = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &a, std::max(n_near, 1)));
+        DDLPB_TRY(ctx_alloc(c, &b, std::max(n_near, 1)));
+        if (n_near > 0) {
+            k_fmm_split_pairs<<<ceil_div(n_near, 256), 256, 0, st>>>(n_near, near, a, b);
+            DDLPB_LAUNCHED(c, "fmm_split_pairs");
+            k_fmm_near_spheres<<<ceil_div(n_near, 256), 256, 0, st>>>(n_near, F.leaf_sphere, a, b);
+            DDLPB_LAUNCHED(c, "fmm_near_spheres");
+        }
+        DDLPB_TRY(fmm_csr(c, a, b, n_near, M, &F.near_ptr, &F.near_j));
+        DDLPB_TRY(fmm_csr(c, b, a, n_near, M, &F.nearT_ptr, &F.nearT_i));
+    }
+    // -- offsets of the coaxial blocks
+    {
+        const int n_tr = n_m2l + 2 * n_nodes;
+        long long *sz = nullptr, *off = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &sz, n_tr + 1));
+        DDLPB_TRY(ctx_alloc(c, &off, n_tr + 1));
+        DDLPB_CK(c, cudaMemsetAsync(sz, 0, sizeof(long long) * (n_tr + 1), st));
+        k_fmm_coax_sizes<<<ceil_div(n_tr, 256), 256, 0, st>>>(n_m2l, n_nodes, p, F.q, F.m2l_s, F.child0, F.parent, sz);
+        DDLPB_LAUNCHED(c, "fmm_coax_sizes");
+        DDLPB_TRY(fmm_scan_ll(c, sz, off, n_tr + 1));
+        DDLPB_CK(c, cudaMemcpyAsync(&F.coax_size, off + n_tr, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        F.coax_off = off;
+        DDLPB_TRY(ctx_alloc(c, &F.m2l_off, std::max(n_m2l, 1)));
+        DDLPB_TRY(ctx_alloc(c, &F.m2m_off, n_nodes));
+        DDLPB_TRY(ctx_alloc(c, &F.l2l_off, n_nodes));
+        k_fmm_coax_offsets<<<ceil_div(n_tr, 256), 256, 0, st>>>(n_m2l, n_nodes, off, F.m2l_off, F.m2m_off, F.l2l_off);
+        DDLPB_LAUNCHED(c, "fmm_coax_offsets");
+        DDLPB_CK(c, cudaStreamSynchronize(st));
+    }
+    return DDLPB_OK;
+}
+
+// Per-precision data: coaxial blocks (FP64 evaluation, stored as T), J, the Y table to degree p,
+// node centres, expansion buffers.
+template <typename T>
+static ddlpb_status fmm_prepare(ddlpb_ctx* c, FmmOps<T>& O) {
+    if (O.ready) return DDLPB_OK;
+    FmmTree& F = c->fmm;
+    const int p = F.p, nbp = (p + 1) * (p + 1);
+    cudaStream_t st = c->stream;
+    // constant tables (host): Gaunt coaxial sums and the rotation J
+    fmmhost::CoaxIndex gi;
+    std::vector<double> g, Jh;
+    fmmhost::gaunt_coax_table(p, gi, g);
+    fmmhost::rotation_J(p, Jh);
+    double* gtab = nullptr;
+    long long* goff = nullptr;
+    DDLPB_TRY(ctx_alloc(c, &gtab, g.size()));
+    DDLPB_TRY(ctx_alloc(c, &goff, gi.off.size()));
+    DDLPB_CK(c, cudaMemcpyAsync(gtab, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, st));
+    DDLPB_CK(c, cudaMemcpyAsync(goff, gi.off.data(), sizeof(long long) * gi.off.size(), cudaMemcpyHostToDevice, st));
+    std::vector<T> Jt(Jh.begin(), Jh.end());
+    DDLPB_TRY(ctx_alloc(c, &O.J, Jt.size()));
+    DDLPB_CK(c, cudaMemcpyAsync(O.J, Jt.data(), sizeof(T) * Jt.size(), cudaMemcpyHostToDevice, st));
+    DDLPB_TRY(ctx_alloc(c, &O.coax, std::max<long long>(F.coax_size, 1)));
+    const int n_tr = F.n_m2l + 2 * F.n_nodes;
+    k_fmm_coax<T><<<n_tr, 128, 0, st>>>(F.n_m2l, F.n_nodes, p, F.q, c->kappa, F.m2l_t, F.m2l_s, F.child0, F.parent,
+                                        F.node_g, gtab, goff, F.coax_off, O.coax);
+    DDLPB_LAUNCHED(c, "fmm_coax");
+    DDLPB_TRY(ctx_alloc(c, &O.Yp, (size_t)c->N * nbp));
+    k_fmm_ytab<T><<<ceil_div(c->N, 128), 128, 0, st>>>(c->N, p, c->leb, c->yt, O.Yp);
+    DDLPB_LAUNCHED(c, "fmm_ytab");
+    DDLPB_TRY(ctx_alloc(c, &O.Mx, (size_t)F.n_nodes * nbp));
+    DDLPB_TRY(ctx_alloc(c, &O.Lx, (size_t)F.n_nodes * nbp));
+    DDLPB_TRY(ctx_alloc(c, &O.part, (size_t)std::max(std::max(F.n_ck, F.n_ckT), 1) * nbp));
+    DDLPB_TRY(ctx_alloc(c, &O.leafq, (size_t)c->M * (F.q + 1) * (F.q + 1)));
+    O.ready = true;
+    return DDLPB_OK;
+}
+
+template <typename T> static FmmOps<T>& fmm_ops(ddlpb_ctx* c);
+template <> FmmOps<double>& fmm_ops<double>(ddlpb_ctx* c) { return c->fmm64; }
+template <> FmmOps<float>& fmm_ops<float>(ddlpb_ctx* c) { return c->fmm32; }
+
+template <typename T>
+static size_t fmm_smem(const FmmTree& F) {
+    const int nbp = (F.p + 1) * (F.p + 1);
+    return sizeof(T) * ((size_t)fmmhost::jblock(F.p + 1) + (size_t)FMM_WARPS * (3 * nbp + 4 * 32));
+}
+
+template <typename T, typename K>
+static ddlpb_status fmm_smem_attr(ddlpb_ctx* c, K kernel, size_t bytes) {
+    if (bytes > 48 * 1024)
+        DDLPB_CK(c, cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return DDLPB_OK;
+}
+
+// phi_ext[t] = sum_j mu_j . (k-ratio basis of sphere j)(x_t) at every external point t: far
+// field by the FMM, near pairs directly.
+template <typename T>
+ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
+    using V4 = typename FmmOps<T>::V4;
+    FmmTree& F = c->fmm;
+    FmmOps<T>& O = fmm_ops<T>(c);
+    DDLPB_TRY(fmm_prepare<T>(c, O));
+    const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax;
+    const long long js = fmmhost::jblock(p + 1);
+    cudaStream_t st = c->stream;
+    const size_t sm = fmm_smem<T>(F);
+    KernelTimer kt(c, "fmm_pot", sizeof(T) == 4);
+    k_fmm_leaf_mult<T><<<M, 128, 0, st>>>(M, c->nb, nbp, F.leaf_node, mu, O.Mx);
+    DDLPB_LAUNCHED(c, "fmm_leaf_mult");
+    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2m<T, V4>, sm)));
+    for (int lv = F.depth - 1; lv >= 0; --lv) {
+        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+        k_fmm_m2m<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(first, count, p, q, js, F.child0,
+                                                                                F.m2m_off, F.node_g, O.J, O.coax, O.Mx);
+        DDLPB_LAUNCHED(c, "fmm_m2m");
+    }
+    if (F.n_ck > 0) {
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l<T, V4>, sm)));
+        k_fmm_m2l<T, V4><<<ceil_div(F.n_ck, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
+            F.n_ck, p, q, js, F.ck_b, F.ck_e, F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.J, O.coax, O.Mx, O.part);
+        DDLPB_LAUNCHED(c, "fmm_m2l");
+    }
+    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_l2l<T, V4>, sm)));
+    for (int lv = 0; lv <= F.depth; ++lv) {
+        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+        k_fmm_l2l<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
+            first, count, p, js, F.parent, F.tck_ptr, O.part, F.l2l_off, F.node_g, O.J, O.coax, O.Lx);
+        DDLPB_LAUNCHED(c, "fmm_l2l");
+    }
+    if (c->E > 0) {
+        const size_t sm2 = sizeof(T) * ((size_t)nbp + (size_t)(L + 1) * 128);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_pot<T, V4>, sm2)));
+        k_fmm_leaf_pot<T, V4><<<M, 128, sm2, st>>>(c->N, c->nb, L, p, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph,
+                                                   c->leb, F.leaf_node, O.Lx, O.Yp, F.near_ptr, F.near_j, mu, S.Khinv,
+                                                   S.yt, phi_ext);
+        DDLPB_LAUNCHED(c, "fmm_leaf_pot");
+    }
+    return DDLPB_OK;
+}
+
+// nu_j = sum_t c_t (k-ratio basis of sphere j)(x_t) over the external points (the transpose of
+// fmm_potential); the far part of sphere j's adjoint to degree q is kept in FmmOps::leafq.
+template <typename T>
+ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
+    using V4 = typename FmmOps<T>::V4;
+    FmmTree& F = c->fmm;
+    FmmOps<T>& O = fmm_ops<T>(c);
+    DDLPB_TRY(fmm_prepare<T>(c, O));
+    const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax, N = c->N;
+    const long long js = fmmhost::jblock(p + 1);
+    cudaStream_t st = c->stream;
+    const size_t sm = fmm_smem<T>(F);
+    KernelTimer kt(c, "fmm_adj", sizeof(T) == 4);
+    const size_t sm0 = (sizeof(T) + sizeof(int)) * (size_t)N;
+    k_fmm_leaf_lambda<T><<<M, 128, sm0, st>>>(N, p, c->ext_ptr, c->ext_p, F.leaf_node, O.Yp, c_ext, O.Lx);
+    DDLPB_LAUNCHED(c, "fmm_leaf_lambda");
+    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_l2l_T<T, V4>, sm)));
+    for (int lv = F.depth - 1; lv >= 0; --lv) {
+        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+        k_fmm_l2l_T<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(first, count, p, js, F.child0,
+                                                                                  F.l2l_off, F.node_g, O.J, O.coax,
+                                                                                  O.Lx);
+        DDLPB_LAUNCHED(c, "fmm_l2l_T");
+    }
+    if (F.n_ckT > 0) {
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_T<T, V4>, sm)));
+        k_fmm_m2l_T<T, V4><<<ceil_div(F.n_ckT, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
+            F.n_ckT, p, q, js, F.ckT_b, F.ckT_e, F.m2lT_k, F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.J,
+            O.coax, O.Lx, O.part);
+        DDLPB_LAUNCHED(c, "fmm_m2l_T");
+    }
+    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2m_T<T, V4>, sm)));
+    for (int lv = 0; lv <= F.depth; ++lv) {
+        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+        k_fmm_m2m_T<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
+            first, count, p, q, js, F.parent, F.child0, F.sck_ptr, O.part, F.m2m_off, F.node_g, O.J, O.coax, O.Mx);
+        DDLPB_LAUNCHED(c, "fmm_m2m_T");
+    }
+    const int nw = 128 / 32;
+    const size_t sm3 = sizeof(T) * ((size_t)nw * c->nb + (L + 2) + (size_t)(L + 1) * 128);
+    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_adj<T, V4>, sm3)));
+    k_fmm_leaf_adj<T, V4><<<M, 128, sm3, st>>>(N, c->nb, L, p, q, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph, c->leb,
+                                               F.leaf_node, O.Mx, F.nearT_ptr, F.nearT_i, c_ext, S.Khinv, S.yt, nu,
+                                               O.leafq);
+    DDLPB_LAUNCHED(c, "fmm_leaf_adj");
+    return DDLPB_OK;
+}
+
+template ddlpb_status fmm_potential<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*);
+template ddlpb_status fmm_potential<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*);
+template ddlpb_status fmm_adjoint<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*);
+template ddlpb_status fmm_adjoint<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*);

@@ -242,6 +242,7 @@ template <typename O> __device__ __forceinline__ O to_store(float v);
 template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
 template <typename O> __device__ __forceinline__ O to_store(double v) { return (O)v; }
+template <> __device__ __forceinline__ __half to_store<__half>(double v) { return __double2half(v); }
 
 // Source position s in [0, H) takes hit order[s] and writes its row at dst[s] (s itself when
 // dst is null) of arrays with row stride `stride`; hps / hjs (when not null) get the hit's
@@ -1094,11 +1095,12 @@ static ddlpb_status build_chunk_copy(ddlpb_ctx* c, OpSet<float>& S, O** Bc, O** 
     DDLPB_TRY(ctx_alloc(c, Rc, (size_t)(L + 1) * H8));
     DDLPB_CK(c, cudaMemsetAsync(*Bc, 0, sizeof(O) * nb * H8, c->stream));
     DDLPB_CK(c, cudaMemsetAsync(*Rc, 0, sizeof(O) * (L + 1) * H8, c->stream));
-    size_t smem = sizeof(float) * 2 * (size_t)(L + 1) * BLK;
-    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<float, float4, O>, smem));
-    k_ab_store<float, float4, O><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
-        (int)H, (long long)H8, c->N, nb, L, (float)c->kappa, S.sph, S.leb, S.yt, c->thit_h, S.tpos, c->hit_p, c->hit_j,
-        S.hit_w, S.Sinv, *Bc, *Rc, nullptr, nullptr);
+    // evaluated in FP64 from the exact geometry and rounded once to the storage type
+    size_t smem = sizeof(double) * 2 * (size_t)(L + 1) * BLK;
+    DDLPB_TRY(set_smem(c, (const void*)k_ab_store<double, double4, O>, smem));
+    k_ab_store<double, double4, O><<<ceil_div(H, BLK), BLK, smem, c->stream>>>(
+        (int)H, (long long)H8, c->N, nb, L, c->kappa, c->sph, c->leb, c->yt, c->thit_h, S.tpos, c->hit_p, c->hit_j,
+        c->hit_w, c->Sinv, *Bc, *Rc, nullptr, nullptr);
     DDLPB_LAUNCHED(c, half ? "ab_store_half" : "ab_store_chunk");
     return DDLPB_OK;
 }
@@ -1267,16 +1269,22 @@ static ddlpb_status yukawa_local_adj_T(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext
     return DDLPB_OK;
 }
 
-// y (+)= [K y ; K y] (forward) or y (+)= [D1 K^T (x_r + x_e) ; D2 K^T (x_r + x_e)] (transpose).
-// With local, K keeps only the sources j in {i} and N_i of each target sphere i.
 template <typename T>
 static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, bool accumulate,
-                              bool local = false) {
+                              bool local = false);
+
+// y (+)= [K y ; K y] (forward) or y (+)= [D1 K^T (x_r + x_e) ; D2 K^T (x_r + x_e)] (transpose).
+// With local, K keeps only the sources j in {i} and N_i of each target sphere i.  With the FMM
+// (fmm_order > 0) the potential and its transpose come from fmm.cu.
+template <typename T>
+static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool transpose, bool accumulate,
+                              bool local) {
     DDLPB_TRY(opset_prepare<T>(c, S));
     const size_t half = (size_t)c->M * c->nb;
     if (!transpose) {
         DDLPB_TRY(source_mu_T<T>(c, S, x, S.mu));
         if (local) DDLPB_TRY(yukawa_local_T<T>(c, S, S.mu, S.extA));
+        else if (c->fmm.on) DDLPB_TRY(fmm_potential<T>(c, S, S.mu, S.extA));
         else DDLPB_TRY(yukawa_pot_T<T>(c, S, S.mu, S.extA));
         DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y, c->nb, accumulate ? 1 : 0));
         DDLPB_TRY(masked_analysis_T<T>(c, S, S.extA, (T)1, nullptr, y + half, c->nb, accumulate ? 1 : 0));
@@ -1286,6 +1294,7 @@ static ddlpb_status apply_C_T(ddlpb_ctx* c, OpSet<T>& S, const T* x, T* y, bool 
     if (c->n_src == 0) return DDLPB_OK;
     DDLPB_TRY(ext_weights_T<T>(c, S, x, S.extA));
     if (local) DDLPB_TRY(yukawa_local_adj_T<T>(c, S, S.extA, S.mu));
+    else if (c->fmm.on) DDLPB_TRY(fmm_adjoint<T>(c, S, S.extA, S.mu));
     else DDLPB_TRY(yukawa_adj_T<T>(c, S, S.extA, S.mu));
     size_t smem = sizeof(T) * (c->nb + c->N) + sizeof(int) * c->N;
     k_ct_finish<T><<<c->n_src, BLK, smem, c->stream>>>(c->M, c->N, c->nb, c->lmax, (T)(c->eps1 / c->eps2), c->src,
@@ -1341,13 +1350,17 @@ ddlpb_status op_source_multipoles(ddlpb_ctx* c, const double* x, double* mu) {
     return source_mu_T<double>(c, c->d64, x, mu);
 }
 
+// The potential of the sphere multipoles mu at the external points and its transpose, in FP64:
+// direct sums, or the FP64 FMM.
 ddlpb_status op_yukawa_potential(ddlpb_ctx* c, const double* mu, double* phi_ext) {
     DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    if (c->fmm.on) return fmm_potential<double>(c, c->d64, mu, phi_ext);
     return yukawa_pot_T<double>(c, c->d64, mu, phi_ext);
 }
 
 ddlpb_status op_yukawa_adjoint(ddlpb_ctx* c, const double* c_ext, double* nu) {
     DDLPB_TRY(opset_prepare<double>(c, c->d64));
+    if (c->fmm.on) return fmm_adjoint<double>(c, c->d64, c_ext, nu);
     return yukawa_adj_T<double>(c, c->d64, c_ext, nu);
 }
 

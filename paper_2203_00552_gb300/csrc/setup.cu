@@ -497,6 +497,9 @@ ddlpb_status ddlpb_internal_setup(ddlpb_ctx* c, const double* centres, const dou
     k_src_fill<<<ceil_div(M, 128), 128, 0, st>>>(M, sflag, spos, c->src);
     DDLPB_LAUNCHED(c, "src_fill");
 
+    // -- FMM tree and interaction lists (far field of the coupling, Appendix)
+    if (c->opt.fmm_order > 0) DDLPB_TRY(fmm_build(c, hc.data()));
+
     // -- vectors and scratch
     c->nvec = 2LL * M * nb;
     const long long half = (long long)M * nb;

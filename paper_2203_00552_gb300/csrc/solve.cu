@@ -75,11 +75,12 @@ __global__ void k_reduce(int G, const double* __restrict__ partial, double* __re
     }
 }
 
-// w -= sum_k V_k h[k]
+// w -= sum_k V_k h[k]  (dynamic shared memory: kk coefficients)
 template <typename T>
 __global__ void k_sub_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ h,
                                   T* __restrict__ w) {
-    __shared__ T sh[512];
+    extern __shared__ unsigned char shraw[];
+    T* sh = (T*)shraw;
     for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)h[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -89,11 +90,12 @@ __global__ void k_sub_combination(long long n, int kk, const T* __restrict__ V, 
     }
 }
 
-// x += sum_k V_k y[k]
+// x += sum_k V_k y[k]  (dynamic shared memory: kk coefficients)
 template <typename T>
 __global__ void k_add_combination(long long n, int kk, const T* __restrict__ V, const double* __restrict__ y,
                                   T* __restrict__ x) {
-    __shared__ T sh[512];
+    extern __shared__ unsigned char shraw[];
+    T* sh = (T*)shraw;
     for (int k = threadIdx.x; k < kk; k += blockDim.x) sh[k] = (T)y[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -293,13 +295,13 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
             DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h1, false));
             {
                 KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
-                k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h1, K.w);
+                k_sub_combination<T><<<VG, VB, sizeof(T) * (k + 1), st>>>(n, k + 1, K.V, h1, K.w);
                 DDLPB_LAUNCHED(c, "sub_comb");
             }
             if (reorth) {
                 DDLPB_TRY(dots<T>(c, K, k + 1, K.V, K.w, h2, false));
                 KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
-                k_sub_combination<T><<<VG, VB, 0, st>>>(n, k + 1, K.V, h2, K.w);
+                k_sub_combination<T><<<VG, VB, sizeof(T) * (k + 1), st>>>(n, k + 1, K.V, h2, K.w);
                 DDLPB_LAUNCHED(c, "sub_comb2");
                 k_add_vec<<<ceil_div(k + 1, 256), 256, 0, st>>>(k + 1, h2, h1);
                 DDLPB_LAUNCHED(c, "add_vec");
@@ -345,7 +347,7 @@ static ddlpb_status gmres_T(ddlpb_ctx* c, Krylov<T>& K, Apply apply, Prec precon
         DDLPB_CK(c, cudaMemcpyAsync(h2, yv.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
         {
             KernelTimer kt(c, "krylov_update", sizeof(T) == 4, 2);
-            k_add_combination<T><<<VG, VB, 0, st>>>(n, k, K.Z ? K.Z : K.V, h2, x);
+            k_add_combination<T><<<VG, VB, sizeof(T) * std::max(k, 1), st>>>(n, k, K.Z ? K.Z : K.V, h2, x);
             DDLPB_LAUNCHED(c, "add_comb");
         }
         DDLPB_CK(c, cudaStreamSynchronize(st));
@@ -540,6 +542,7 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->kernel_timing = 0;
     o->precond_coupling = 0;
     o->precond_fp16 = 1;
+    o->fmm_theta = 0.5;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,
@@ -567,9 +570,11 @@ static ddlpb_status setup_common(int n, const double* centres, const double* rad
     if (!(o.eta > 0.0 && o.eta <= 1.0)) return fail("eta must be in (0, 1]");
     if (!(o.tol > 0.0)) return fail("tol must be > 0");
     if (o.max_iter < 1) return fail("max_iter must be >= 1");
-    if (o.gmres_restart < 1 || o.gmres_restart > 400) return fail("gmres_restart must be in [1, 400]");
+    if (o.gmres_restart < 1 || o.gmres_restart > 2000) return fail("gmres_restart must be in [1, 2000]");
     if (o.precision != DDLPB_FP64 && o.precision != DDLPB_MIXED) return fail("unknown precision");
-    if (o.fmm_order != 0) return fail("fmm_order must be 0 (direct summation)");
+    if (o.fmm_order != 0 && (o.fmm_order < lmax + 1 || o.fmm_order > DDLPB_FMM_PMAX))
+        return fail("fmm_order must be 0 (direct summation) or in [lmax + 1, 22]");
+    if (o.fmm_order != 0 && !(o.fmm_theta > 0.0 && o.fmm_theta < 1.0)) return fail("fmm_theta must be in (0, 1)");
     if (!(o.precond_tol > 0.0 && o.precond_tol <= 1.0)) return fail("precond_tol must be in (0, 1]");
     ddlpb_ctx* c = new ddlpb_ctx();
     c->M = n;
