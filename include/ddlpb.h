@@ -213,9 +213,8 @@ DDLPB_API const char* ddlpb_last_setup_error(void);
 /*
  * Energy without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they need the
- * energy (for example code running inside a captured stream or a host callback, or an
- * engine whose own allocator owns all device memory and which already holds the
- * solution vector X).
+ * energy (an engine whose own allocator owns all device memory, or an MD driver that
+ * already holds the solution vector X and hands the library only that).
  *   n        number of atoms, 1 <= n <= 1048576 (the size of the library's static
  *            scratch: 4097 doubles); larger n returns DDLPB_EINVAL
  *   lmax     degree of the expansions of X, 0 <= lmax <= 16
@@ -223,15 +222,17 @@ DDLPB_API const char* ddlpb_last_setup_error(void);
  *   X        device pointer to the solution [X_r ; X_e] in the layout of
  *            ddlpb_get_vector_device (only the X_r block is read)
  *   e        receives E_s = 1/2 sum_j q_j Y_00 X_r[j, 00] (Hartree); host or device memory
- *   cuda_stream  stream to run on (NULL: legacy default stream); the call returns
- *            after the result is in *e
+ *   cuda_stream  stream to run on (NULL: legacy default stream); the call synchronises
+ *            this stream and returns after the result is in *e, so it cannot be used
+ *            inside a stream capture or a host callback
  * The scratch is a fixed device array shared by every call in the process; it keeps
  * the last call's contents, so calls that overlap on the GPU (other threads, other
  * streams) race and must be serialised by the caller.  The first call on each device
- * looks up the array's device address (with that device current); make that first call
- * before any stream capture.  Nothing is allocated: no cudaMalloc, no cudaFree.
- * Errors: DDLPB_EINVAL (NULL pointer, n or lmax out of range), DDLPB_ECUDA; the message
- * is in ddlpb_noalloc_last_error().
+ * looks up the array's device address (with that device current) and keeps it for the
+ * life of the process (the device's primary context must not be reset in between).
+ * Nothing is allocated: no cudaMalloc, no cudaFree.
+ * Errors: DDLPB_EINVAL (NULL pointer, n or lmax out of range, device index above 63),
+ * DDLPB_ECUDA; the message is in ddlpb_noalloc_last_error().
  */
 DDLPB_API ddlpb_status ddlpb_energy_noalloc(int n, int lmax, const double* charges, const double* X, double* e,
                                             void* cuda_stream);

@@ -150,6 +150,8 @@ struct FmmOps {
     T* Lx = nullptr;          // [n_nodes][(p+1)^2] locals (transposed pass: their adjoints)
     T* part = nullptr;        // [max(n_ck, n_ckT)][(p+1)^2] partial sums of the chunks
     T* leafq = nullptr;       // [M][(q+1)^2] adjoint of the leaf multipoles to degree q
+    double* grad = nullptr;   // gradient map of the real basis (fmm_host.h), FP64 set only
+    long long* grad_off = nullptr;
 };
 
 // Scratch of the force assembly, allocated on the first ddlpb_forces call.
@@ -593,3 +595,6 @@ ddlpb_status op_apply_fp32(ddlpb_ctx* c, int op, const double* x, double* y);
 ddlpb_status fmm_build(ddlpb_ctx* c, const double* host_centres);
 template <typename T> ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext);
 template <typename T> ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu);
+// Yukawa force terms with the FMM (target side added to Ft, source side to G); needs the
+// transposed pass of the same c_t = fs[t].w to have run last.
+ddlpb_status fmm_force_terms(ddlpb_ctx* c, const double* mu, const double4* fs, double* Ft, double* G);

@@ -1207,3 +1207,214 @@ template ddlpb_status fmm_potential<double>(ddlpb_ctx*, OpSet<double>&, const do
 template ddlpb_status fmm_potential<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*);
 template ddlpb_status fmm_adjoint<double>(ddlpb_ctx*, OpSet<double>&, const double*, double*);
 template ddlpb_status fmm_adjoint<float>(ddlpb_ctx*, OpSet<float>&, const float*, float*);
+
+// ---------------------------------------------------------------- force terms (FP64)
+
+// Target side of the Yukawa force terms: Ft[t] += c_t grad phi(x_t) at every external point t of
+// sphere i, phi the potential of mu from every sphere j != i: the far field from i's local
+// expansion (its gradient on the sphere: dR_l Y s + (grad_S Y)/r_i, R_l = 1 at rho = r_i) and the
+// near sources directly.
+__global__ void k_fmm_force_targets(int N, int nb, int L, int p, double kappa, const int* __restrict__ ext_ptr,
+                                    const int* __restrict__ ext_p, const double4* __restrict__ sph,
+                                    const double4* __restrict__ leb, const int* __restrict__ leaf_node,
+                                    const double* __restrict__ Lx, const int* __restrict__ near_ptr,
+                                    const int* __restrict__ near_j, const double* __restrict__ mu,
+                                    const double* __restrict__ Khinv, YTab yt, const double4* __restrict__ fs,
+                                    double* __restrict__ Ft) {
+    extern __shared__ double fsm[];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    const int nbp = (p + 1) * (p + 1);
+    const int i = blockIdx.x;
+    const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+    if (cnt == 0) return;
+    double* Li = fsm;
+    double* dR = Li + nbp;
+    double* rad = dR + (p + 2);
+    double* drad = rad + (size_t)(L + 1) * bd;
+    const double4 a = sph[i];
+    for (int k = tid; k < nbp; k += bd) Li[k] = Lx[(size_t)leaf_node[i] * nbp + k];
+    // d/drho of i_l(kappa rho)/i_l(kappa r_i) at rho = r_i
+    for (int l = tid; l <= p; l += bd) {
+        const double x = kappa * a.w;
+        dR[l] = (double)l / a.w + kappa * kappa * a.w / (double)(2 * l + 3) * scaled_i_series<double>(l + 1, x) /
+                                      scaled_i_series<double>(l, x);
+    }
+    __syncthreads();
+    const int k0 = near_ptr[i], k1 = near_ptr[i + 1];
+    for (int t = t0 + tid; t < t0 + cnt; t += bd) {
+        const int n = ext_p[t] % N;
+        const double4 s = leb[n];
+        double A = 0, Bx = 0, By = 0, Bz = 0;
+        ylm_grad_stream<double>(p, s.x, s.y, s.z, yt, [&](int idx, int l, double yv, double gx, double gy, double gz) {
+            const double cl = Li[idx];
+            A += cl * dR[l] * yv;
+            Bx += cl * gx;
+            By += cl * gy;
+            Bz += cl * gz;
+        });
+        const double pr = Bx * s.x + By * s.y + Bz * s.z, ir = 1.0 / a.w;
+        double gx = A * s.x + (Bx - pr * s.x) * ir, gy = A * s.y + (By - pr * s.y) * ir, gz = A * s.z + (Bz - pr * s.z) * ir;
+        for (int kk = k0; kk < k1; ++kk) {
+            const int j = near_j[kk];
+            if (j == i) continue;
+            const double4 b = sph[j];
+            const double dx = a.x - b.x + a.w * s.x, dy = a.y - b.y + a.w * s.y, dz = a.z - b.z + a.w * s.z;
+            const double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
+            const double ex = dx * inv, ey = dy * inv, ez = dz * inv;
+            radial<double>(2, L, rho, b.w, kappa, Khinv + (size_t)j * (L + 2), rad + tid, drad + tid, bd);
+            const double* m = mu + (size_t)j * nb;
+            double Aa = 0, Cx = 0, Cy = 0, Cz = 0;
+            ylm_grad_stream<double>(L, ex, ey, ez, yt, [&](int idx, int l, double yv, double hx, double hy, double hz) {
+                const double cc = m[idx];
+                Aa += cc * drad[tid + l * bd] * yv;
+                const double fr = cc * rad[tid + l * bd] * inv;
+                Cx += fr * hx;
+                Cy += fr * hy;
+                Cz += fr * hz;
+            });
+            const double pq = Cx * ex + Cy * ey + Cz * ez;
+            gx += Aa * ex + Cx - pq * ex;
+            gy += Aa * ey + Cy - pq * ey;
+            gz += Aa * ez + Cz - pq * ez;
+        }
+        const double ct = fs[t].w;
+        Ft[3 * (size_t)t] += ct * gx;
+        Ft[3 * (size_t)t + 1] += ct * gy;
+        Ft[3 * (size_t)t + 2] += ct * gz;
+    }
+}
+
+// Source side: G[j] -= sum_{t not on j} c_t grad (mu_j . B_j)(x_t).  Far part: the adjoint of
+// the leaf multipole to degree q (leafq, from the transposed pass with the same c_t) contracted
+// with the gradient map of the k-ratio basis (degrees l -> l +- 1); near targets directly.
+__global__ void k_fmm_force_sources(int N, int nb, int L, int q, double kappa, const int* __restrict__ ext_ptr,
+                                    const int* __restrict__ ext_p, const double4* __restrict__ sph,
+                                    const double4* __restrict__ leb, const int* __restrict__ nearT_ptr,
+                                    const int* __restrict__ nearT_i, const double* __restrict__ mu,
+                                    const double* __restrict__ Khinv, YTab yt, const double4* __restrict__ fs,
+                                    const double* __restrict__ leafq, const double* __restrict__ gtab,
+                                    const long long* __restrict__ goff, double* __restrict__ G) {
+    extern __shared__ double fsm[];
+    const int bd = blockDim.x, tid = threadIdx.x;
+    const int j = blockIdx.x;
+    if (ext_ptr[j + 1] == ext_ptr[j]) return;   // no external points: mu_j = 0
+    const int nq = (q + 1) * (q + 1);
+    double* m = fsm;
+    double* kh = m + nb;
+    double* rad = kh + (L + 2);
+    double* drad = rad + (size_t)(L + 1) * bd;
+    double* red = drad + (size_t)(L + 1) * bd;
+    const double4 b = sph[j];
+    for (int k = tid; k < nb; k += bd) m[k] = mu[(size_t)j * nb + k];
+    for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
+    __syncthreads();
+    double fx = 0, fy = 0, fz = 0;
+    // far part: input (l, m) per thread
+    const double x = kappa * b.w;
+    const double* Q = leafq + (size_t)j * nq;
+    for (int idx = tid; idx < nb; idx += bd) {
+        const int l = (int)sqrtf((float)idx + 0.5f), mi = idx - l * l;
+        const double cm = m[idx];
+        for (int up = 1; up >= 0; --up) {
+            const int lp = up ? l + 1 : l - 1;
+            if (lp < 0 || lp > q) continue;
+            // -kappa k_lp(kappa r_j) / k_l(kappa r_j) with k_l = (2l-1)!! exp(-x) khat_l(x) / x^(l+1)
+            const double ratio = up ? -kappa * (2.0 * l + 1.0) * kh[l] / (kh[l + 1] * x)
+                                    : -kappa * x * kh[l] / ((2.0 * l - 1.0) * kh[l - 1]);
+            const int n = 2 * l + 1, np = 2 * lp + 1;
+            const double* T = gtab + goff[(size_t)l * 2 + up];
+            const double* qv = Q + lp * lp;
+            double sx = 0, sy = 0, sz = 0;
+            for (int c = 0; c < np; ++c) {
+                sx += T[((size_t)0 * n + mi) * np + c] * qv[c];
+                sy += T[((size_t)1 * n + mi) * np + c] * qv[c];
+                sz += T[((size_t)2 * n + mi) * np + c] * qv[c];
+            }
+            fx += cm * ratio * sx;
+            fy += cm * ratio * sy;
+            fz += cm * ratio * sz;
+        }
+    }
+    // near targets t on spheres i != j of j's near list
+    for (int kk = nearT_ptr[j]; kk < nearT_ptr[j + 1]; ++kk) {
+        const int i = nearT_i[kk];
+        if (i == j) continue;
+        const double4 a = sph[i];
+        const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
+        for (int base = 0; base < cnt; base += bd) {
+            const bool ok = base + tid < cnt;
+            const int t = t0 + base + tid;
+            double dx = b.w, dy = 0, dz = 0, ct = 0;
+            if (ok) {
+                const double4 s = leb[ext_p[t] % N];
+                dx = a.x - b.x + a.w * s.x;
+                dy = a.y - b.y + a.w * s.y;
+                dz = a.z - b.z + a.w * s.z;
+                ct = fs[t].w;
+            }
+            const double rho = sqrt(dx * dx + dy * dy + dz * dz), inv = 1.0 / rho;
+            const double ex = dx * inv, ey = dy * inv, ez = dz * inv;
+            radial<double>(2, L, rho, b.w, kappa, kh, rad + tid, drad + tid, bd);
+            double Aa = 0, Cx = 0, Cy = 0, Cz = 0;
+            ylm_grad_stream<double>(L, ex, ey, ez, yt, [&](int idx, int l, double yv, double hx, double hy, double hz) {
+                const double cc = m[idx];
+                Aa += cc * drad[tid + l * bd] * yv;
+                const double fr = cc * rad[tid + l * bd] * inv;
+                Cx += fr * hx;
+                Cy += fr * hy;
+                Cz += fr * hz;
+            });
+            const double pq = Cx * ex + Cy * ey + Cz * ez;
+            fx += ct * (Aa * ex + Cx - pq * ex);
+            fy += ct * (Aa * ey + Cy - pq * ey);
+            fz += ct * (Aa * ez + Cz - pq * ez);
+        }
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if ((tid & 31) == 0) {
+        red[3 * (tid >> 5)] = fx;
+        red[3 * (tid >> 5) + 1] = fy;
+        red[3 * (tid >> 5) + 2] = fz;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double s = 0;
+        for (int w = 0; w < bd / 32; ++w) s += red[3 * w + tid];
+        G[3 * (size_t)j + tid] -= s;
+    }
+}
+
+// The Yukawa force terms with the FMM (FP64): target side into Ft, source side into G.  The
+// caller has run the transposed pass with c_t = fs[t].w (FmmOps::leafq holds its far part).
+ddlpb_status fmm_force_terms(ddlpb_ctx* c, const double* mu, const double4* fs, double* Ft, double* G) {
+    FmmTree& F = c->fmm;
+    FmmOps<double>& O = c->fmm64;
+    const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax;
+    cudaStream_t st = c->stream;
+    if (!O.grad) {
+        fmmhost::GradIndex gi;
+        std::vector<double> tab;
+        fmmhost::gradient_table(L, gi, tab);
+        DDLPB_TRY(ctx_alloc(c, &O.grad, tab.size()));
+        DDLPB_TRY(ctx_alloc(c, &O.grad_off, gi.off.size()));
+        DDLPB_CK(c, cudaMemcpyAsync(O.grad, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+        DDLPB_CK(c, cudaMemcpyAsync(O.grad_off, gi.off.data(), sizeof(long long) * gi.off.size(), cudaMemcpyHostToDevice,
+                                    st));
+    }
+    // leaf locals of mu (the potential itself goes to scratch)
+    DDLPB_TRY(fmm_potential<double>(c, c->d64, mu, c->extA));
+    const size_t sm1 = sizeof(double) * ((size_t)nbp + (p + 2) + 2 * (size_t)(L + 1) * 128);
+    DDLPB_TRY((fmm_smem_attr<double>(c, k_fmm_force_targets, sm1)));
+    k_fmm_force_targets<<<M, 128, sm1, st>>>(c->N, c->nb, L, p, c->kappa, c->ext_ptr, c->ext_p, c->sph, c->leb,
+                                              F.leaf_node, O.Lx, F.near_ptr, F.near_j, mu, c->Khinv, c->yt, fs, Ft);
+    DDLPB_LAUNCHED(c, "fmm_force_targets");
+    const size_t sm2 = sizeof(double) * ((size_t)c->nb + (L + 2) + 2 * (size_t)(L + 1) * 128 + 3 * 4);
+    DDLPB_TRY((fmm_smem_attr<double>(c, k_fmm_force_sources, sm2)));
+    k_fmm_force_sources<<<M, 128, sm2, st>>>(c->N, c->nb, L, q, c->kappa, c->ext_ptr, c->ext_p, c->sph, c->leb,
+                                              F.nearT_ptr, F.nearT_i, mu, c->Khinv, c->yt, fs, O.leafq, O.grad,
+                                              O.grad_off, G);
+    DDLPB_LAUNCHED(c, "fmm_force_sources");
+    return DDLPB_OK;
+}

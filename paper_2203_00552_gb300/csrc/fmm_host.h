@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <vector>
 
 namespace fmmhost {
@@ -164,6 +165,108 @@ inline long long coax_block_size(int pin, int pout) {
     long long s = 0;
     for (int m = 0; m <= std::min(pin, pout); ++m) s += (long long)(pin + 1 - m) * (pout + 1 - m);
     return s;
+}
+
+// Gradient of f_l(r) Y_lm in the real basis (used for the source-side force terms of the FMM):
+//   d_alpha (f_l Y_lm) = sum_m' c[alpha][l -> l+1][m][m'] g+ Y_{l+1,m'} + c[alpha][l -> l-1][m][m'] g- Y_{l-1,m'},
+// g+ = f' - l f / r, g- = f' + (l+1) f / r (for f = k_l(kappa r): g+ = -kappa k_{l+1}, g- = -kappa k_{l-1}).
+// The coefficients follow from the textbook gradient formula of the complex harmonics with the
+// Condon-Shortley phase (z component and the ladder combinations d_x +- i d_y), converted to the
+// library's real basis: R_l0 = Y_l^0, R_lm = ((-1)^m Y_l^m + Y_l^-m)/sqrt(2),
+// R_l,-m = ((-1)^m Y_l^m - Y_l^-m)/(i sqrt(2)), m > 0.
+// Layout: for l = 0..L, for the two targets lp = l+1 and lp = l-1 (the latter absent at l = 0),
+// for alpha = x, y, z, a (2l+1) x (2lp+1) block (row: the input m, column: the output m').
+struct GradIndex {
+    int L = 0;
+    std::vector<long long> off;   // [(L+1) * 2]: block triple of (l, up) (up = 1: lp = l+1), -1 if absent
+    long long size = 0;
+};
+
+inline void gradient_table(int L, GradIndex& gi, std::vector<double>& tab) {
+    typedef std::complex<double> cd;
+    gi.L = L;
+    gi.off.assign((size_t)(L + 1) * 2, -1);
+    long long o = 0;
+    for (int l = 0; l <= L; ++l)
+        for (int up = 1; up >= 0; --up) {
+            const int lp = up ? l + 1 : l - 1;
+            if (lp < 0) continue;
+            gi.off[(size_t)l * 2 + up] = o;
+            o += 3LL * (2 * l + 1) * (2 * lp + 1);
+        }
+    gi.size = o;
+    tab.assign((size_t)o, 0.0);
+    auto Umat = [](int l) {   // real <- complex, rows real m' + l, columns complex m + l
+        const int n = 2 * l + 1;
+        std::vector<cd> U((size_t)n * n, cd(0.0, 0.0));
+        U[(size_t)l * n + l] = 1.0;
+        const double s = 1.0 / std::sqrt(2.0);
+        for (int m = 1; m <= l; ++m) {
+            const double sg = (m & 1) ? -1.0 : 1.0;
+            U[(size_t)(l + m) * n + (l + m)] = sg * s;
+            U[(size_t)(l + m) * n + (l - m)] = s;
+            U[(size_t)(l - m) * n + (l + m)] = sg * s / cd(0.0, 1.0);
+            U[(size_t)(l - m) * n + (l - m)] = -s / cd(0.0, 1.0);
+        }
+        return U;
+    };
+    auto inv_U = [](int l) {   // complex <- real (U is unitary)
+        const int n = 2 * l + 1;
+        std::vector<cd> V((size_t)n * n, cd(0.0, 0.0));
+        V[(size_t)l * n + l] = 1.0;
+        const double s = 1.0 / std::sqrt(2.0);
+        for (int m = 1; m <= l; ++m) {
+            const double sg = (m & 1) ? -1.0 : 1.0;
+            // Y^m = sg (R_m + i R_-m)/sqrt2, Y^-m = (R_m - i R_-m)/sqrt2
+            V[(size_t)(l + m) * n + (l + m)] = sg * s;
+            V[(size_t)(l + m) * n + (l - m)] = sg * s * cd(0.0, 1.0);
+            V[(size_t)(l - m) * n + (l + m)] = s;
+            V[(size_t)(l - m) * n + (l - m)] = -s * cd(0.0, 1.0);
+        }
+        return V;
+    };
+    for (int l = 0; l <= L; ++l)
+        for (int up = 1; up >= 0; --up) {
+            const int lp = up ? l + 1 : l - 1;
+            if (lp < 0) continue;
+            const int n = 2 * l + 1, np = 2 * lp + 1;
+            std::vector<cd> Gc((size_t)3 * n * np, cd(0.0, 0.0));   // complex: rows m, columns m'
+            for (int m = -l; m <= l; ++m) {
+                double z, pl, mi;
+                if (up) {
+                    const double den = (2.0 * l + 1) * (2.0 * l + 3);
+                    z = std::sqrt(((l + 1.0) * (l + 1.0) - (double)m * m) / den);
+                    pl = -std::sqrt((l + m + 1.0) * (l + m + 2.0) / den);
+                    mi = std::sqrt((l - m + 1.0) * (l - m + 2.0) / den);
+                } else {
+                    const double den = (2.0 * l - 1) * (2.0 * l + 1);
+                    z = std::sqrt(((double)l * l - (double)m * m) / den);
+                    pl = std::sqrt(std::max(0.0, (l - m) * (l - m - 1.0)) / den);
+                    mi = -std::sqrt(std::max(0.0, (l + m) * (l + m - 1.0)) / den);
+                }
+                auto at = [&](int a, int mm) -> cd& { return Gc[((size_t)a * n + (m + l)) * np + (mm + lp)]; };
+                if (std::abs(m) <= lp) at(2, m) += z;
+                if (std::abs(m + 1) <= lp) {   // (d_x + i d_y) -> Y^{m+1}
+                    at(0, m + 1) += pl / 2.0;
+                    at(1, m + 1) += pl / cd(0.0, 2.0);
+                }
+                if (std::abs(m - 1) <= lp) {   // (d_x - i d_y) -> Y^{m-1}
+                    at(0, m - 1) += mi / 2.0;
+                    at(1, m - 1) -= mi / cd(0.0, 2.0);
+                }
+            }
+            const std::vector<cd> U = Umat(l), Vp = inv_U(lp);
+            double* out = tab.data() + gi.off[(size_t)l * 2 + up];
+            for (int a = 0; a < 3; ++a)
+                for (int r = 0; r < n; ++r)
+                    for (int cc = 0; cc < np; ++cc) {
+                        cd s(0.0, 0.0);
+                        for (int k = 0; k < n; ++k)
+                            for (int q = 0; q < np; ++q)
+                                s += U[(size_t)r * n + k] * Gc[((size_t)a * n + k) * np + q] * Vp[(size_t)q * np + cc];
+                        out[((size_t)a * n + r) * np + cc] = s.real();
+                    }
+        }
 }
 
 }  // namespace fmmhost

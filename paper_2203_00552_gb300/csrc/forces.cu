@@ -473,17 +473,22 @@ ddlpb_status compute_forces(ddlpb_ctx* c, double* f_dev) {
                      sizeof(double) * (FT_TS * (size_t)nb + FT_TS * (size_t)(L + 2) + 2 * (size_t)(L + 1) * FB);
         sm3 = std::max(sm3, sizeof(double4) * FB);
         DDLPB_TRY(fsmem(c, (const void*)k_force_targets, sm3));
+        // with the FMM the Yukawa part is added below (far field from the expansions), so
+        // this kernel keeps only the Coulomb part (no sources)
         k_force_targets<<<ceil_div(c->E, FB), FB, sm3, st>>>(c->E, N, M, nb, L, c->kappa, c->eps1, c->ext_x,
-                                                             c->ext_p, c->leb, c->n_src, c->src, c->sph, c->q, s.muc,
-                                                             c->Khinv, c->yt, s.fs, s.Ft);
+                                                             c->ext_p, c->leb, c->fmm.on ? 0 : c->n_src, c->src,
+                                                             c->sph, c->q, s.muc, c->Khinv, c->yt, s.fs, s.Ft);
         DDLPB_LAUNCHED(c, "force_targets");
+        if (c->fmm.on) DDLPB_TRY(fmm_force_terms(c, s.muc, s.fs, s.Ft, s.G));
         k_force_targets_gather<<<M, FB, 0, st>>>(c->ext_ptr, s.Ft, s.G);
         DDLPB_LAUNCHED(c, "force_targets_gather");
-        size_t sm4 = sizeof(double) * (nb + (L + 2) + 2 * (size_t)(L + 1) * FB + 3 * (FB / 32));
-        DDLPB_TRY(fsmem(c, (const void*)k_force_yukawa_sources, sm4));
-        k_force_yukawa_sources<<<c->n_src, FB, sm4, st>>>(c->E, N, nb, L, c->kappa, c->ext_x, c->ext_p, c->src,
-                                                          c->sph, s.muc, c->Khinv, c->yt, s.fs, s.G);
-        DDLPB_LAUNCHED(c, "force_yukawa_sources");
+        if (!c->fmm.on) {
+            size_t sm4 = sizeof(double) * (nb + (L + 2) + 2 * (size_t)(L + 1) * FB + 3 * (FB / 32));
+            DDLPB_TRY(fsmem(c, (const void*)k_force_yukawa_sources, sm4));
+            k_force_yukawa_sources<<<c->n_src, FB, sm4, st>>>(c->E, N, nb, L, c->kappa, c->ext_x, c->ext_p, c->src,
+                                                              c->sph, s.muc, c->Khinv, c->yt, s.fs, s.G);
+            DDLPB_LAUNCHED(c, "force_yukawa_sources");
+        }
         k_force_coulomb_sources<<<M, FB, 0, st>>>(c->E, N, c->eps1, c->ext_x, c->ext_p, c->leb, c->sph, c->q, s.fs,
                                                   s.G);
         DDLPB_LAUNCHED(c, "force_coulomb_sources");

@@ -1,12 +1,18 @@
 // noalloc.cu -- an energy entry point that performs no device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need the
-// solvation energy: code running inside a host callback or between kernels of a
-// captured stream, custom allocators that forbid cudaMalloc, or an MD engine that
-// owns all device memory and hands the library only the solution vector it
-// already holds.  For them ddlpb_energy_noalloc computes the energy from caller
-// buffers, using as scratch a fixed file-scope device array instead of memory of
-// its own.
+// solvation energy: an engine whose own allocator owns all device memory (and
+// forbids cudaMalloc behind its back), or an MD driver that hands the library only
+// the solution vector it already holds.  For them ddlpb_energy_noalloc computes the
+// energy from caller buffers, using as scratch a fixed file-scope device array
+// instead of memory of its own.  The call ends with a synchronisation of the
+// caller's stream (the result is in *e on return), so it is not for use inside a
+// stream capture or a host callback.
+//
+// The device address of the array is looked up once per device index and kept for
+// the life of the process; this assumes the device's primary context (the one the
+// runtime uses) is not reset in between (after cudaDeviceReset the cached address
+// would be stale).
 #include <mutex>
 
 #include "common.cuh"
@@ -75,9 +81,13 @@ extern "C" ddlpb_status ddlpb_energy_noalloc(int n, int lmax, const double* char
     }
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+    if (err != cudaSuccess) {
         g_na_err = std::string("cudaGetDevice: ") + cudaGetErrorString(err);
         return DDLPB_ECUDA;
+    }
+    if (dev < 0 || dev >= NA_MAX_DEVICES) {
+        g_na_err = "device index " + std::to_string(dev) + " exceeds " + std::to_string(NA_MAX_DEVICES - 1);
+        return DDLPB_EINVAL;
     }
     double* scratch = nullptr;
     {

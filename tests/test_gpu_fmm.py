@@ -91,6 +91,20 @@ def test_fmm_energy_matches_oracle_fmm(fcase):
     assert abs(E - E0) <= 1e-10 * abs(E0), (E, E0)
 
 
+def test_fmm_forces_match_oracle_fmm(fcase):
+    """Forces in FMM mode: the target-side gradients of the local expansions and the source-side
+    gradients through the degree lmax + 1 adjoint (Appendix), near pairs directly; the oracle
+    computes the same from its projection-based translations and a projected gradient map."""
+    P, ctx = fcase["P"], fcase["ctx"]
+    P.solve()
+    P.adjoint()
+    F0 = P.forces()
+    ctx.solve()
+    ctx.adjoint()
+    F = ctx.forces()
+    assert np.abs(F - F0).max() <= 1e-8, np.abs(F - F0).max()
+
+
 def test_fmm_mixed_matches_fp64_fmm():
     """The mixed form (FP32 FMM inside the Krylov solves, FP64 residuals) on a 200-atom globule at
     lmax 6, p = 8, against the FP64 FMM path on the same input, both solved to the workloads'
@@ -100,7 +114,12 @@ def test_fmm_mixed_matches_fp64_fmm():
     a = G.Context(c, r, q, EPS, KAPPA, 6, 110, **kw)
     a.solve()
     E64 = a.energy()
+    a.adjoint()
+    F64 = a.forces()
     b = G.Context(c, r, q, EPS, KAPPA, 6, 110, precision=G.DDLPB_MIXED, **kw)
     b.solve()
     Em = b.energy()
+    b.adjoint()
+    Fm = b.forces()
     assert abs(Em - E64) <= 1e-6 * abs(E64), (Em, E64)
+    assert np.linalg.norm(Fm - F64) <= 1e-5 * np.linalg.norm(F64)
