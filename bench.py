@@ -1,12 +1,12 @@
 """Benchmark: ddLPB energy + analytical forces, atoms/s.
 
-Default workload (named in config.workload): `globule1000_sas`, the 1000-atom globule grown
-by the chain rule inside an 18 A ball (seed 1), SAS radii (U[1.2, 2.0] A + 1.4 A probe),
-charges U[-0.5, 0.5] e with zero net charge, eps = 78.54, kappa = 0.104 1/A, lmax = 8,
-302-point Lebedev grid, outer tolerance 1e-8 (FP64 relative residual).  The 10,000-atom
-globule (lmax 10, 590 points; `--workload globule10000`) fits one GPU but its solves do not
-converge within a bench run (near-singular local modes of the dense synthetic cluster at
-lmax 10, with the coupling summed directly), so the default line uses the 1000-atom one.
+Default workload (named in config.workload): `globule1000_sas`, the 1000-atom globule (chain
+growth rule, then compacted onto the 18 A ball, seed 1), SAS radii (U[1.2, 2.0] A + 1.4 A
+probe), charges U[-0.5, 0.5] e with zero net charge, eps = 78.54, kappa = 0.104 1/A, lmax = 8,
+302-point Lebedev grid, the coupling's far field by the FMM of order 16, outer tolerance 1e-8
+(FP64 relative residual).  The 10,000-atom globule (lmax 10, 590 points, FMM order 20;
+`--workload globule10000`) fits one GPU, but its preconditioned system needs thousands of
+Krylov iterations (their count grows with the atom count and lmax), far beyond a bench run.
 One step = setup (neighbour lists, switch functions, hit lists, right-hand side) + primal
 solve + adjoint solve + energy + forces, from inputs already resident in HBM.  The mixed
 form runs the Krylov solves in FP32 inside FP64 iterative refinement; --precision fp64
@@ -40,7 +40,8 @@ FP32_PEAK_TFLOPS_AT_MAX_CLOCK = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 la
 # Algorithmic FP32 flops per unit of the hot kernels (see the kernel roofline table):
 #   per (hit, basis function) for the A/B kernels (two bases, 8 flops each),
 #   per (target, source, basis function) for the Yukawa kernels.
-FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8}
+FLOPS_PER_UNIT = {"ab_apply": 16, "ab_transpose": 16, "yukawa_pot": 8, "yukawa_adj": 8,
+                  "fmm_m2l": 1, "fmm_m2l_T": 1}   # the FMM translations count their flops themselves
 HBM_PEAK_GBS = 6789.6   # measured copy bandwidth of this machine's GB300 (read + write bytes)
 # dram bytes per launch from the committed ncu capture (profiles/), keyed by (kernel, workload),
 # with the digest of the kernel's source text they were taken on; null once that text changes.
@@ -53,7 +54,8 @@ KERNEL_SOURCES = {"ab_apply_f32": ["load8_f", "load8", "k_ab_hits_chunk"],
 # every group of launches the library times at kernel_timing = 2 (setup and forces as one group each)
 BREAKDOWN_NAMES = ([b + sfx for b in ("ab_apply", "ab_transpose", "yukawa_pot", "yukawa_adj", "krylov_dot",
                                       "krylov_update", "ab_project", "synthesis", "masked_analysis",
-                                      "coupling_projection", "store") for sfx in ("_f16", "_f32", "_f64")]
+                                      "coupling_projection", "store", "fmm_m2l", "fmm_m2l_T", "fmm_tree",
+                                      "fmm_near") for sfx in ("_f16", "_f32", "_f64")]
                    + ["setup_f64", "forces_f64"])
 
 
@@ -67,6 +69,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=300)
     ap.add_argument("--precond-tol", type=float, default=0.4)
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fmm-order", type=int, default=None,
+                    help="FMM expansion order (default: the workload's; 0 = direct summation)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the instrumented breakdown step")
@@ -227,7 +231,9 @@ def main():
             pg.barrier()
     G.library()
     prec = G.DDLPB_MIXED if args.precision == "mixed" else G.DDLPB_FP64
-    opts = dict(tol=1e-8, precision=prec, gmres_restart=args.restart, precond_tol=args.precond_tol, max_iter=4000)
+    fmm_order = w["fmm_order"] if args.fmm_order is None else args.fmm_order
+    opts = dict(tol=1e-8, precision=prec, gmres_restart=args.restart, precond_tol=args.precond_tol, max_iter=4000,
+                fmm_order=fmm_order)
     M = w["n"]
     cen = torch.tensor(w["centres"], device=dev)
     rad = torch.tensor(w["radii"], device=dev)
@@ -371,7 +377,8 @@ def main():
     nb = (w["lmax"] + 1) ** 2
     units = {"ab_apply": info["n_hits"] * nb, "ab_transpose": info["n_hits"] * nb,
              "yukawa_pot": info["n_external"] * info["n_sources"] * nb,
-             "yukawa_adj": info["n_external"] * info["n_sources"] * nb}
+             "yukawa_adj": info["n_external"] * info["n_sources"] * nb,
+             "fmm_m2l": info["fmm_m2l_flops"], "fmm_m2l_T": info["fmm_m2l_flops"]}
     roofline = None
     L = w["lmax"]
     # The stored A/B products of the FP32 set stream the basis (HBM-bound): algorithmic bytes
@@ -409,9 +416,11 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if prec == G.DDLPB_MIXED else "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f16+f32+f64" if prec == G.DDLPB_MIXED else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "atoms": M, "lmax": w["lmax"], "n_lebedev": w["n_lebedev"],
-                           "surface": w["surface"], "precision": args.precision, "coupling": "direct summation",
+                           "surface": w["surface"], "precision": args.precision,
+                           "coupling": ("fmm" if fmm_order > 0 else "direct summation"), "fmm_order": fmm_order,
+                           "fmm_theta": 0.5 if fmm_order > 0 else None,
                            "tol": 1e-8, "gmres_restart": args.restart, "precond_tol": args.precond_tol,
                            "l2": "512 MB buffer written between timed steps; working set > L2",
                            "parallelism": "replicas" if world > 1 else "single"},
@@ -420,7 +429,8 @@ def main():
                 "solver": {"outer": info["solve_iterations"], "adjoint_outer": info["adjoint_iterations"],
                            "refinement": info["refinement_steps"], "residual": info["solve_residual"],
                            "adjoint_residual": info["adjoint_residual"], "external_points": info["n_external"],
-                           "hits": info["n_hits"], "sources": info["n_sources"]},
+                           "hits": info["n_hits"], "sources": info["n_sources"], "fmm_m2l": info["fmm_m2l"],
+                           "fmm_near_pairs": info["fmm_near_pairs"], "fmm_nodes": info["fmm_nodes"]},
                 "energy_hartree": float(e_out.item())}
         print(json.dumps(line), flush=True)
     if pg:

@@ -67,7 +67,7 @@ typedef struct {
     int gmres_restart;   /* Krylov basis size before restart, 1..2000; default 150 (the preconditioned
                             spectrum is real but spread, so short restarts stagnate) */
     int precision;       /* ddlpb_precision; default DDLPB_FP64 */
-    int fmm_order;       /* 0: direct summation of the dense coupling; p in [lmax + 1, 22]: its far field
+    int fmm_order;       /* 0: direct summation of the dense coupling; p in [lmax + 1, 21]: its far field
                             by the fast multipole method of the Appendix with expansions of order p
                             (binary tree over the Morton-ordered spheres, single-sphere leaves,
                             near pairs summed directly); default 0 */
@@ -105,6 +105,11 @@ typedef struct {
     int inner_iterations;          /* inner A/B Krylov iterations of the last solve (preconditioner) */
     int n_sources;                 /* spheres with at least one external point (sources of the coupling) */
     long long kernel_launches;     /* CUDA kernels this context has launched since setup began */
+    long long fmm_nodes;           /* FMM tree nodes (0 without the FMM) */
+    long long fmm_m2l;             /* M2L translations of one FMM pass */
+    long long fmm_near_pairs;      /* (target sphere, source sphere) pairs summed directly */
+    double fmm_m2l_flops;          /* arithmetic of the M2L translations of one pass (rotations with the
+                                      J table and the coaxial products, 2 flops per multiply-add) */
 } ddlpb_info;
 
 /* Fill *opt with the defaults listed above. */

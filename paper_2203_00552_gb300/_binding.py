@@ -38,7 +38,8 @@ class Info(C.Structure):
                 ("solve_iterations", C.c_int), ("adjoint_iterations", C.c_int), ("solve_residual", C.c_double),
                 ("adjoint_residual", C.c_double), ("refinement_steps", C.c_int),
                 ("inner_iterations", C.c_int), ("n_sources", C.c_int),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("fmm_nodes", C.c_longlong), ("fmm_m2l", C.c_longlong),
+                ("fmm_near_pairs", C.c_longlong), ("fmm_m2l_flops", C.c_double)]
 
 
 class DDLPBError(RuntimeError):

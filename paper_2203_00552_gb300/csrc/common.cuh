@@ -15,7 +15,7 @@
 #include "ddlpb.h"
 
 #define DDLPB_LMAX_MAX 16
-#define DDLPB_FMM_PMAX 22               // highest FMM expansion order (J of degree p in shared memory)
+#define DDLPB_FMM_PMAX 21               // highest FMM expansion order (J of degree p in shared memory)
 #define DDLPB_LT 32                     // row stride of the (l, m) coefficient tables (degrees <= 31)
 #define DDLPB_TCHUNK 512                // hits per CTA of the transposed A/B product
 
@@ -144,7 +144,8 @@ struct FmmOps {
     using V4 = typename V4T<T>::type;
     bool ready = false;
     T* coax = nullptr;        // [coax_size] coaxial translation blocks
-    T* J = nullptr;           // rotation about x by -90 degrees, degree by degree
+    T* JP = nullptr;          // rotation about x by -90 degrees, degree blocks padded to multiples of 4
+    long long jpsize = 0;
     T* Yp = nullptr;          // [N][(p+1)^2] Y_lm(s_n), l <= p
     T* Mx = nullptr;          // [n_nodes][(p+1)^2] multipoles (transposed pass: their adjoints)
     T* Lx = nullptr;          // [n_nodes][(p+1)^2] locals (transposed pass: their adjoints)

@@ -41,7 +41,6 @@
 #include "common.cuh"
 #include "fmm_host.h"
 
-#define FMM_WARPS 4
 
 // ---------------------------------------------------------------- tree construction
 
@@ -227,6 +226,13 @@ __global__ void k_fmm_coax_sizes(int n_m2l, int n_nodes, int p, int q, const int
     }
 }
 
+// Number of M2L translations whose source is a leaf (input degree q instead of p).
+__global__ void k_fmm_count_leaf_src(int n, const int* __restrict__ m2l_s, const int* __restrict__ child0,
+                                     int* __restrict__ cnt) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n && child0[m2l_s[u]] < 0) atomicAdd(cnt, 1);
+}
+
 __global__ void k_fmm_coax_offsets(int n_m2l, int n_nodes, const long long* __restrict__ off,
                                    long long* __restrict__ m2l_off, long long* __restrict__ m2m_off,
                                    long long* __restrict__ l2l_off) {
@@ -332,144 +338,7 @@ __global__ void k_fmm_ytab(int N, int p, const double4* __restrict__ leb, YTab y
     ylm_stream<double>(p, s.x, s.y, s.z, yt, [&](int idx, int, double v) { Yp[(size_t)n * nbp + idx] = (T)v; });
 }
 
-// ---------------------------------------------------------------- warp translations
-
 __device__ __forceinline__ int deg_of(int idx) { return (int)sqrtf((float)idx + 0.5f); }
-
-// Per-warp scratch: two coefficient vectors and the angle tables cos/sin(m alpha), cos/sin(m beta).
-template <typename T>
-struct WarpScratch {
-    T* v;
-    T* w;
-    T* ca;
-    T* sa;
-    T* cb;
-    T* sb;
-};
-
-// Rotation about z of the coefficients of degree <= deg: Rz(s * angle) with the angle's
-// cos/sin(m angle) tables (s = +1 or -1).
-template <typename T>
-__device__ __forceinline__ void rot_z(T* v, int deg, const T* cm, const T* sm, T s, int lane) {
-    for (int idx = lane; idx < (deg + 1) * (deg + 1); idx += 32) {
-        const int l = deg_of(idx), m = idx - l * l - l;
-        if (m <= 0) continue;
-        const T c = cm[m], sn = s * sm[m];
-        const T a = v[idx], b = v[idx - 2 * m];
-        v[idx] = c * a - sn * b;
-        v[idx - 2 * m] = sn * a + c * b;
-    }
-    __syncwarp();
-}
-
-// out = J in (or J^T in), degree by degree, degree <= deg.
-template <typename T>
-__device__ __forceinline__ void rot_J(const T* __restrict__ J, const T* in, T* out, int deg, bool tr, int lane) {
-    for (int idx = lane; idx < (deg + 1) * (deg + 1); idx += 32) {
-        const int l = deg_of(idx), mi = idx - l * l, n = 2 * l + 1;
-        const T* Jl = J + (long long)l * (4LL * l * l - 1) / 3;
-        const T* x = in + l * l;
-        T s = 0;
-        if (tr) {
-            for (int mj = 0; mj < n; ++mj) s += Jl[mj * n + mi] * x[mj];
-        } else {
-            const T* row = Jl + mi * n;
-            for (int mj = 0; mj < n; ++mj) s += row[mj] * x[mj];
-        }
-        out[idx] = s;
-    }
-    __syncwarp();
-}
-
-// Coaxial step of a translation with forward degrees (pin -> pout): forward out = Z in (out
-// degree pout), transposed out = Z^T in (out degree pin).
-template <typename T>
-__device__ __forceinline__ void coax_apply(const T* __restrict__ Z, int pin, int pout, bool tr, const T* in, T* out,
-                                           int lane) {
-    const int dout = tr ? pin : pout;
-    for (int idx = lane; idx < (dout + 1) * (dout + 1); idx += 32) {
-        const int o = deg_of(idx), m = idx - o * o - o, am = m < 0 ? -m : m;
-        T s = 0;
-        if (am <= min(pin, pout)) {
-            long long bo = 0;
-            for (int mm = 0; mm < am; ++mm) bo += (long long)(pin + 1 - mm) * (pout + 1 - mm);
-            const int na = pout + 1 - am;
-            const T* blk = Z + bo;
-            if (!tr) {   // o = a: sum over input degrees l
-                for (int l = am; l <= pin; ++l) s += blk[(l - am) * na + (o - am)] * in[l * l + l + m];
-            } else {     // o = l: sum over output degrees a
-                const T* row = blk + (long long)(o - am) * na;
-                for (int a = am; a <= pout; ++a) s += row[a - am] * in[a * a + a + m];
-            }
-        }
-        out[idx] = s;
-    }
-    __syncwarp();
-}
-
-// Angle tables of the translation vector t (cos/sin of m alpha and m beta, m <= p).
-template <typename T>
-__device__ __forceinline__ void angles(T tx, T ty, T tz, int p, WarpScratch<T>& ws, int lane) {
-    const T rxy = sqrt(tx * tx + ty * ty);
-    const T alpha = rxy > (T)0 ? atan2(ty, tx) : (T)0;
-    const T beta = atan2(rxy, tz);
-    if (lane <= p) {
-        T s, c;
-        if constexpr (sizeof(T) == 8) {
-            sincos((double)lane * alpha, &s, &c);
-        } else {
-            sincosf((float)lane * alpha, &s, &c);
-        }
-        ws.ca[lane] = c;
-        ws.sa[lane] = s;
-        if constexpr (sizeof(T) == 8) {
-            sincos((double)lane * beta, &s, &c);
-        } else {
-            sincosf((float)lane * beta, &s, &c);
-        }
-        ws.cb[lane] = c;
-        ws.sb[lane] = s;
-    }
-    __syncwarp();
-}
-
-// One translation by the warp.  Forward: ws.v holds the input (degree pin), the result (degree
-// pout) is left in ws.w.  Transposed: ws.v holds degree pout, the result (degree pin) in ws.w.
-template <typename T>
-__device__ __forceinline__ void translate(const T* __restrict__ J, const T* __restrict__ Z, int pin, int pout,
-                                          bool tr, WarpScratch<T>& ws, int lane) {
-    const int d1 = tr ? pout : pin, d2 = tr ? pin : pout;
-    rot_z(ws.v, d1, ws.ca, ws.sa, (T)-1, lane);      // Rz(-alpha)
-    rot_J(J, ws.v, ws.w, d1, true, lane);            // J^T
-    rot_z(ws.w, d1, ws.cb, ws.sb, (T)-1, lane);      // Rz(-beta)
-    rot_J(J, ws.w, ws.v, d1, false, lane);           // J
-    coax_apply(Z, pin, pout, tr, ws.v, ws.w, lane);  // along z
-    rot_J(J, ws.w, ws.v, d2, true, lane);            // J^T
-    rot_z(ws.v, d2, ws.cb, ws.sb, (T)1, lane);       // Rz(beta)
-    rot_J(J, ws.v, ws.w, d2, false, lane);           // J
-    rot_z(ws.w, d2, ws.ca, ws.sa, (T)1, lane);       // Rz(alpha)
-}
-
-// Shared memory of a translation kernel: J, then per warp v, w (nbp each), acc (nbp), 4 (p+1) angles.
-template <typename T>
-__device__ __forceinline__ WarpScratch<T> warp_scratch(T* sm, long long jsize, int nbp, int warp, T** acc) {
-    T* base = sm + jsize + (long long)warp * (3 * nbp + 4 * 32);
-    WarpScratch<T> ws;
-    ws.v = base;
-    ws.w = base + nbp;
-    *acc = base + 2 * nbp;
-    ws.ca = base + 3 * nbp;
-    ws.sa = ws.ca + 32;
-    ws.cb = ws.sa + 32;
-    ws.sb = ws.cb + 32;
-    return ws;
-}
-
-template <typename T>
-__device__ __forceinline__ void load_J(T* sm, const T* __restrict__ J, long long jsize) {
-    for (long long k = threadIdx.x; k < jsize; k += blockDim.x) sm[k] = J[k];
-    __syncthreads();
-}
 
 // ---------------------------------------------------------------- forward pass
 
@@ -480,102 +349,6 @@ __global__ void k_fmm_leaf_mult(int M, int nb, int nbp, const int* __restrict__ 
     const int j = blockIdx.x;
     T* out = Mx + (size_t)leaf_node[j] * nbp;
     for (int k = threadIdx.x; k < nbp; k += blockDim.x) out[k] = k < nb ? mu[(size_t)j * nb + k] : (T)0;
-}
-
-// M2M into the internal nodes [first, first + count) of one level: M_P = sum_c M2M(c -> P) M_c.
-template <typename T, typename V4>
-__global__ void k_fmm_m2m(int first, int count, int p, int q, long long jsize, const int* __restrict__ child0,
-                          const long long* __restrict__ m2m_off, const double4* __restrict__ nc, const T* __restrict__ J,
-                          const T* __restrict__ coax, T* __restrict__ Mx) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int k = first + blockIdx.x * FMM_WARPS + warp;
-    if (k >= first + count) return;
-    const int c0 = child0[k];
-    if (c0 < 0) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    const double4 P = nc[k];
-    for (int c = c0; c <= c0 + 1; ++c) {
-        const int pin = child0[c] < 0 ? q : p;
-        const double4 C = nc[c];
-        angles<T>((T)(P.x - C.x), (T)(P.y - C.y), (T)(P.z - C.z), p, ws, lane);
-        const T* src = Mx + (size_t)c * nbp;
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = i < (pin + 1) * (pin + 1) ? src[i] : (T)0;
-        __syncwarp();
-        translate(sm, coax + m2m_off[c], pin, p, false, ws, lane);
-        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
-        __syncwarp();
-    }
-    for (int i = lane; i < nbp; i += 32) Mx[(size_t)k * nbp + i] = acc[i];
-}
-
-// M2L, one warp per chunk of the target-sorted list; the chunk's sum goes to part[chunk].
-template <typename T, typename V4>
-__global__ void k_fmm_m2l(int n_ck, int p, int q, long long jsize, const int* __restrict__ ck_b,
-                          const int* __restrict__ ck_e, const int* __restrict__ m2l_t, const int* __restrict__ m2l_s,
-                          const long long* __restrict__ m2l_off, const int* __restrict__ child0,
-                          const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
-                          const T* __restrict__ Mx, T* __restrict__ part) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int ck = blockIdx.x * FMM_WARPS + warp;
-    if (ck >= n_ck) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    for (int u = ck_b[ck]; u < ck_e[ck]; ++u) {
-        const int A = m2l_t[u], B = m2l_s[u];
-        const int pin = child0[B] < 0 ? q : p;
-        const double4 ca = nc[A], cb = nc[B];
-        angles<T>((T)(ca.x - cb.x), (T)(ca.y - cb.y), (T)(ca.z - cb.z), p, ws, lane);
-        const T* src = Mx + (size_t)B * nbp;
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = i < (pin + 1) * (pin + 1) ? src[i] : (T)0;
-        __syncwarp();
-        translate(sm, coax + m2l_off[u], pin, p, false, ws, lane);
-        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
-        __syncwarp();
-    }
-    for (int i = lane; i < nbp; i += 32) part[(size_t)ck * nbp + i] = acc[i];
-}
-
-// Locals of the nodes [first, first + count) of one level: L_C = sum of C's M2L chunks +
-// L2L(parent -> C) L_parent.
-template <typename T, typename V4>
-__global__ void k_fmm_l2l(int first, int count, int p, long long jsize, const int* __restrict__ parent,
-                          const int* __restrict__ tck_ptr, const T* __restrict__ part,
-                          const long long* __restrict__ l2l_off, const double4* __restrict__ nc, const T* __restrict__ J,
-                          const T* __restrict__ coax, T* __restrict__ Lx) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int k = first + blockIdx.x * FMM_WARPS + warp;
-    if (k >= first + count) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    for (int ck = tck_ptr[k]; ck < tck_ptr[k + 1]; ++ck)
-        for (int i = lane; i < nbp; i += 32) acc[i] += part[(size_t)ck * nbp + i];
-    const int P = parent[k];
-    if (P >= 0) {
-        const double4 cc = nc[k], cp = nc[P];
-        angles<T>((T)(cc.x - cp.x), (T)(cc.y - cp.y), (T)(cc.z - cp.z), p, ws, lane);
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)P * nbp + i];
-        __syncwarp();
-        translate(sm, coax + l2l_off[k], p, p, false, ws, lane);
-        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
-    }
-    __syncwarp();
-    for (int i = lane; i < nbp; i += 32) Lx[(size_t)k * nbp + i] = acc[i];
 }
 
 // Potential at the external points of target sphere i: the leaf local (sum L_lm Y_lm(s_n)) plus
@@ -648,104 +421,6 @@ __global__ void k_fmm_leaf_lambda(int N, int p, const int* __restrict__ ext_ptr,
     }
 }
 
-// Transposed L2L, one level: Lambda_P = sum_c L2L(P -> c)^T Lambda_c for the internal nodes.
-template <typename T, typename V4>
-__global__ void k_fmm_l2l_T(int first, int count, int p, long long jsize, const int* __restrict__ child0,
-                            const long long* __restrict__ l2l_off, const double4* __restrict__ nc,
-                            const T* __restrict__ J, const T* __restrict__ coax, T* __restrict__ Lx) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int k = first + blockIdx.x * FMM_WARPS + warp;
-    if (k >= first + count) return;
-    const int c0 = child0[k];
-    if (c0 < 0) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    const double4 P = nc[k];
-    for (int c = c0; c <= c0 + 1; ++c) {
-        const double4 C = nc[c];
-        angles<T>((T)(C.x - P.x), (T)(C.y - P.y), (T)(C.z - P.z), p, ws, lane);
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)c * nbp + i];
-        __syncwarp();
-        translate(sm, coax + l2l_off[c], p, p, true, ws, lane);
-        for (int i = lane; i < nbp; i += 32) acc[i] += ws.w[i];
-        __syncwarp();
-    }
-    for (int i = lane; i < nbp; i += 32) Lx[(size_t)k * nbp + i] = acc[i];
-}
-
-// Transposed M2L, one warp per chunk of the source-sorted view: part[chunk] = sum of
-// M2L(B -> A)^T Lambda_A over the chunk (degree of B's multipole).
-template <typename T, typename V4>
-__global__ void k_fmm_m2l_T(int n_ck, int p, int q, long long jsize, const int* __restrict__ ck_b,
-                            const int* __restrict__ ck_e, const int* __restrict__ m2lT_k,
-                            const int* __restrict__ m2l_t, const int* __restrict__ m2l_s,
-                            const long long* __restrict__ m2l_off, const int* __restrict__ child0,
-                            const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
-                            const T* __restrict__ Lx, T* __restrict__ part) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int ck = blockIdx.x * FMM_WARPS + warp;
-    if (ck >= n_ck) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    for (int v = ck_b[ck]; v < ck_e[ck]; ++v) {
-        const int u = m2lT_k[v];
-        const int A = m2l_t[u], B = m2l_s[u];
-        const int pin = child0[B] < 0 ? q : p;
-        const double4 ca = nc[A], cb = nc[B];
-        angles<T>((T)(ca.x - cb.x), (T)(ca.y - cb.y), (T)(ca.z - cb.z), p, ws, lane);
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = Lx[(size_t)A * nbp + i];
-        __syncwarp();
-        translate(sm, coax + m2l_off[u], pin, p, true, ws, lane);
-        for (int i = lane; i < (pin + 1) * (pin + 1); i += 32) acc[i] += ws.w[i];
-        __syncwarp();
-    }
-    for (int i = lane; i < nbp; i += 32) part[(size_t)ck * nbp + i] = acc[i];
-}
-
-// Adjoint multipoles of the nodes [first, first + count) of one level: Psi_C = sum of C's
-// transposed M2L chunks + M2M(C -> parent)^T Psi_parent.
-template <typename T, typename V4>
-__global__ void k_fmm_m2m_T(int first, int count, int p, int q, long long jsize, const int* __restrict__ parent,
-                            const int* __restrict__ child0, const int* __restrict__ sck_ptr,
-                            const T* __restrict__ part, const long long* __restrict__ m2m_off,
-                            const double4* __restrict__ nc, const T* __restrict__ J, const T* __restrict__ coax,
-                            T* __restrict__ Mx) {
-    extern __shared__ unsigned char smraw[];
-    T* sm = (T*)smraw;
-    load_J(sm, J, jsize);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbp = (p + 1) * (p + 1);
-    const int k = first + blockIdx.x * FMM_WARPS + warp;
-    if (k >= first + count) return;
-    T* acc;
-    WarpScratch<T> ws = warp_scratch(sm, jsize, nbp, warp, &acc);
-    for (int i = lane; i < nbp; i += 32) acc[i] = 0;
-    for (int ck = sck_ptr[k]; ck < sck_ptr[k + 1]; ++ck)
-        for (int i = lane; i < nbp; i += 32) acc[i] += part[(size_t)ck * nbp + i];
-    const int P = parent[k];
-    if (P >= 0) {
-        const int pin = child0[k] < 0 ? q : p;
-        const double4 cc = nc[k], cp = nc[P];
-        angles<T>((T)(cp.x - cc.x), (T)(cp.y - cc.y), (T)(cp.z - cc.z), p, ws, lane);
-        for (int i = lane; i < nbp; i += 32) ws.v[i] = Mx[(size_t)P * nbp + i];
-        __syncwarp();
-        translate(sm, coax + m2m_off[k], pin, p, true, ws, lane);
-        for (int i = lane; i < (pin + 1) * (pin + 1); i += 32) acc[i] += ws.w[i];
-    }
-    __syncwarp();
-    for (int i = lane; i < nbp; i += 32) Mx[(size_t)k * nbp + i] = acc[i];
-}
-
 // nu_j = (far adjoint of the leaf multipole, l <= lmax) + sum over the near targets t of
 // sphere j's near list of c_t k-ratio basis of j at x_t.  Also keeps the far part to degree q.
 // Spheres without external points are no sources of the coupling (P chi_j = 0): their rows of
@@ -800,6 +475,400 @@ __global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, cons
     }
     if (leafq)
         for (int idx = tid; idx < nq; idx += bd) leafq[(size_t)j * nq + idx] = far[idx];
+}
+
+// ---------------------------------------------------------------- batched translations
+//
+// A CTA translates FMM_TB expansions at a time.  Every rotation about x by -90 degrees is then
+// a small matrix product J_l [n x n] x [n x FMM_TB] per degree l, tiled 4 rows x 4 translations
+// per thread (each J entry read from shared memory serves 4 translations, each coefficient 4
+// rows).  J sits in shared memory with every degree block zero-padded to n4 x n4 (n4 = n rounded
+// up to 4), row-major, so that the 4 rows of a tile of J^T are one contiguous load.  The coaxial
+// step reads each translation's stored block once (consecutive threads on consecutive output
+// degrees), one load serving +m and -m.  Used by the M2L chunks (FP32 and FP64) and by the tree
+// passes (M2M, L2L and their transposes, a few nodes per CTA).
+
+#define FMM_TB 8          // translations in shared memory at a time
+#define FMM_BT 256        // threads of a batched CTA
+// shared-memory head of a batched CTA: per translation the block offset (long long), input
+// degree, source row, valid flag (int); degree tables (int); rounded up to 16 bytes
+#define FMM_BATCH_HEAD ((8 * FMM_TB + 4 * (3 * FMM_TB + 3 * (DDLPB_FMM_PMAX + 4)) + 15) / 16 * 16)
+
+struct BatchHead {
+    long long* zoff;   // [TB] coaxial block of translation b
+    int* pin;          // [TB] input degree (forward direction) of translation b
+    int* row;          // [TB] row of the input vector (node index), -1: no translation
+    int* rgoff;        // [p+2] row groups of 4 below degree l
+    int* jpoff;        // [p+2] offset of the padded J block of degree l (in elements)
+    int* bo;           // [p+2] scratch
+};
+
+__device__ __forceinline__ BatchHead batch_head(unsigned char* sm) {
+    BatchHead h;
+    h.zoff = (long long*)sm;
+    h.pin = (int*)(h.zoff + FMM_TB);
+    h.row = h.pin + FMM_TB;
+    h.rgoff = h.row + FMM_TB;
+    h.jpoff = h.rgoff + DDLPB_FMM_PMAX + 4;
+    h.bo = h.jpoff + DDLPB_FMM_PMAX + 4;
+    return h;
+}
+
+__device__ __forceinline__ void fill_tables(const BatchHead& h, int p) {
+    if (threadIdx.x == 0) {
+        h.rgoff[0] = 0;
+        h.jpoff[0] = 0;
+        for (int l = 0; l <= p; ++l) {
+            const int n4 = (2 * l + 1 + 3) / 4 * 4;
+            h.rgoff[l + 1] = h.rgoff[l] + n4 / 4;
+            h.jpoff[l + 1] = h.jpoff[l] + n4 * n4;
+        }
+    }
+}
+
+// Rz(s angle_b) on the whole batch, degree <= deg; ang[b][which][cos|sin][32].
+template <typename T>
+__device__ __forceinline__ void brot_z(T* V, int nbp, int deg, const T* ang, int which, T s) {
+    const int nd = (deg + 1) * (deg + 1);
+    for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
+        const int l = deg_of(idx), m = idx - l * l - l;
+        if (m <= 0) continue;
+#pragma unroll
+        for (int b = 0; b < FMM_TB; ++b) {
+            const T* a = ang + (b * 4 + which * 2) * 32;
+            const T c = a[m], sn = s * a[32 + m];
+            T* v = V + (size_t)b * nbp;
+            const T x = v[idx], y = v[idx - 2 * m];
+            v[idx] = c * x - sn * y;
+            v[idx - 2 * m] = sn * x + c * y;
+        }
+    }
+    __syncthreads();
+}
+
+// Out[b] = J In[b] (or J^T In[b]) degree by degree, degree <= deg, all FMM_TB rows.
+template <typename T>
+__device__ __forceinline__ void bmul_J(const T* __restrict__ JP, const T* In, T* Out, int nbp, int deg, bool tr,
+                                       const BatchHead& h) {
+    const int R = h.rgoff[deg + 1];
+    for (int e = threadIdx.x; e < R * (FMM_TB / 4); e += blockDim.x) {
+        const int cg = e / R, r = e - cg * R;
+        int l = 0;
+        while (h.rgoff[l + 1] <= r) ++l;
+        const int n = 2 * l + 1, n4 = (n + 3) & ~3, r0 = 4 * (r - h.rgoff[l]), b0 = 4 * cg;
+        const T* Jl = JP + h.jpoff[l];
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+        const T* x0 = In + (size_t)b0 * nbp + l * l;
+        if (tr) {
+            const T* col = Jl + r0;
+            for (int k = 0; k < n; ++k) {
+                T jv[4], xv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) jv[i] = col[k * n4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv[j] = x0[(size_t)j * nbp + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += jv[i] * xv[j];
+            }
+        } else {
+            const T* rows = Jl + r0 * n4;
+            for (int k = 0; k < n; ++k) {
+                T jv[4], xv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) jv[i] = rows[i * n4 + k];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv[j] = x0[(size_t)j * nbp + k];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += jv[i] * xv[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T* o = Out + (size_t)(b0 + j) * nbp + l * l;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (r0 + i < n) o[r0 + i] = acc[i][j];
+        }
+    }
+    __syncthreads();
+}
+
+// Offset of the order-m part of a coaxial block with degrees (pin -> pout):
+// sum_{k < m} (pin + 1 - k)(pout + 1 - k), in closed form.
+__device__ __forceinline__ long long coax_m_offset(int pin, int pout, int m) {
+    const long long A = pin + 1, B = pout + 1, M = m;
+    return M * A * B - (A + B) * M * (M - 1) / 2 + (M - 1) * M * (2 * M - 1) / 6;
+}
+
+// Coaxial step (forward degrees pin_b -> pout): forward Out = Z_b In (degree pout), transposed
+// Out = Z_b^T In (degree pin_b).  Rows without a translation are skipped (their Out is zero).
+// The stored block is read from global memory 8 entries at a time per thread (independent loads
+// in flight) before the multiply-adds.
+template <typename T>
+__device__ __forceinline__ void bcoax(const T* __restrict__ coax, const BatchHead& h, int pout, bool tr, const T* In,
+                                      T* Out, int nbp) {
+    for (int i = threadIdx.x; i < FMM_TB * nbp; i += blockDim.x) Out[i] = 0;
+    __syncthreads();
+    const int per_b = (pout + 1) * (pout + 1);
+    for (int e = threadIdx.x; e < FMM_TB * per_b; e += blockDim.x) {
+        const int b = e / per_b, r = e - b * per_b;
+        if (h.row[b] < 0) continue;
+        const int pb = h.pin[b];
+        const int m = r / (pout + 1), o = r - m * (pout + 1);
+        if (m > min(pb, pout) || o < m || (tr && o > pb)) continue;
+        const int na = pout + 1 - m;
+        const T* Z = coax + h.zoff[b] + coax_m_offset(pb, pout, m);
+        const T* x = In + (size_t)b * nbp;
+        T sp = 0, sm = 0;
+        // forward: z_k = Z[(k - m) na + (o - m)], coefficient index k over input degrees l;
+        // transposed: z_k = Z[(o - m) na + (k - m)], k over output degrees a
+        const int kend = tr ? pout : pb;
+        const long long zs = tr ? 1 : na;
+        const T* zp = tr ? Z + (long long)(o - m) * na : Z + (o - m);
+        for (int k0 = m; k0 <= kend; k0 += 8) {
+            T z[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) z[u] = (k0 + u <= kend) ? __ldg(zp + (long long)(k0 + u - m) * zs) : (T)0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u;
+                if (k <= kend) {
+                    sp += z[u] * x[k * k + k + m];
+                    sm += z[u] * x[k * k + k - m];
+                }
+            }
+        }
+        T* y = Out + (size_t)b * nbp;
+        y[o * o + o + m] = sp;
+        if (m > 0) y[o * o + o - m] = sm;
+    }
+    __syncthreads();
+}
+
+// Angle tables of translation b from the FP64 node centres (t = target - source).
+template <typename T>
+__device__ __forceinline__ void batch_angles(T* ang, int b, int lane, int p, const double4& ct, const double4& cs) {
+    const T tx = (T)(ct.x - cs.x), ty = (T)(ct.y - cs.y), tz = (T)(ct.z - cs.z);
+    const T rxy = sqrt(tx * tx + ty * ty);
+    const T alpha = rxy > (T)0 ? atan2(ty, tx) : (T)0;
+    const T beta = atan2(rxy, tz);
+    if (lane <= p) {
+        T s, c;
+        T* a = ang + b * 128;
+        if constexpr (sizeof(T) == 8) sincos((double)lane * alpha, &s, &c);
+        else sincosf((float)lane * alpha, &s, &c);
+        a[lane] = c;
+        a[32 + lane] = s;
+        if constexpr (sizeof(T) == 8) sincos((double)lane * beta, &s, &c);
+        else sincosf((float)lane * beta, &s, &c);
+        a[64 + lane] = c;
+        a[96 + lane] = s;
+    }
+}
+
+// Translate the batch in place: V holds the inputs (rows b, degree d1), W receives the outputs
+// (degree d2).  TR: the transposed translations.
+template <typename T>
+__device__ __forceinline__ void batch_translate(const T* JP, const T* coax, const BatchHead& h, const T* ang, int p,
+                                                bool tr, int d1, int d2, T* V, T* W, int nbp) {
+    brot_z(V, nbp, d1, ang, 0, (T)-1);           // Rz(-alpha)
+    bmul_J(JP, V, W, nbp, d1, true, h);          // J^T
+    brot_z(W, nbp, d1, ang, 1, (T)-1);           // Rz(-beta)
+    bmul_J(JP, W, V, nbp, d1, false, h);         // J
+    bcoax(coax, h, p, tr, V, W, nbp);            // along z
+    bmul_J(JP, W, V, nbp, d2, true, h);          // J^T
+    brot_z(V, nbp, d2, ang, 1, (T)1);            // Rz(beta)
+    bmul_J(JP, V, W, nbp, d2, false, h);         // J
+    brot_z(W, nbp, d2, ang, 0, (T)1);            // Rz(alpha)
+}
+
+// Shared-memory layout of a batched CTA after the head: JP, V, W, acc, angles.
+template <typename T>
+struct BatchArrays {
+    T* JP;
+    T* V;
+    T* W;
+    T* acc;
+    T* ang;
+};
+
+template <typename T>
+__device__ __forceinline__ BatchArrays<T> batch_arrays(unsigned char* sm, long long jpsize, int nbp, int nacc) {
+    BatchArrays<T> a;
+    a.JP = (T*)(sm + FMM_BATCH_HEAD);
+    a.V = a.JP + jpsize;
+    a.W = a.V + (size_t)FMM_TB * nbp;
+    a.acc = a.W + (size_t)FMM_TB * nbp;
+    a.ang = a.acc + (size_t)nacc * nbp;
+    return a;
+}
+
+template <typename T>
+__device__ __forceinline__ void batch_setup(const BatchArrays<T>& a, const BatchHead& h, const T* __restrict__ JPg,
+                                            long long jpsize, int p) {
+    for (long long k = threadIdx.x; k < jpsize; k += blockDim.x) a.JP[k] = JPg[k];
+    fill_tables(h, p);
+}
+
+// Load the batch's input rows (zero above their degree and for absent translations).
+template <typename T>
+__device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restrict__ X, T* V, int nbp, int din_tr,
+                                           bool tr) {
+    for (int e = threadIdx.x; e < FMM_TB * nbp; e += blockDim.x) {
+        const int b = e / nbp, i = e - b * nbp;
+        const int rw = h.row[b];
+        const int dl = tr ? din_tr : h.pin[b];
+        V[e] = (rw >= 0 && i < (dl + 1) * (dl + 1)) ? X[(size_t)rw * nbp + i] : (T)0;
+    }
+    __syncthreads();
+}
+
+// M2L, one CTA per chunk.  Forward: the chunk's translations share the target; part[ck] = their
+// sum (degree p).  Transposed: they share the source; part[ck] = the sum of the transposed
+// translations of the targets' local adjoints (degree of the source's multipole).
+template <typename T, bool TR>
+__global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q, long long jpsize,
+                                                          const int* __restrict__ ck_b, const int* __restrict__ ck_e,
+                                                          const int* __restrict__ perm, const int* __restrict__ m2l_t,
+                                                          const int* __restrict__ m2l_s,
+                                                          const long long* __restrict__ m2l_off,
+                                                          const int* __restrict__ child0,
+                                                          const double4* __restrict__ nc, const T* __restrict__ JPg,
+                                                          const T* __restrict__ coax, const T* __restrict__ X,
+                                                          T* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nbp = (p + 1) * (p + 1);
+    const BatchHead h = batch_head(smraw);
+    const BatchArrays<T> a = batch_arrays<T>(smraw, jpsize, nbp, 1);
+    batch_setup(a, h, JPg, jpsize, p);
+    for (int i = threadIdx.x; i < nbp; i += blockDim.x) a.acc[i] = 0;
+    const int ck = blockIdx.x;
+    const int u0 = ck_b[ck], u1 = ck_e[ck];
+    __syncthreads();
+    for (int ub = u0; ub < u1; ub += FMM_TB) {
+        const int nt = min(FMM_TB, u1 - ub);
+        {
+            const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;   // FMM_BT / 32 == FMM_TB
+            if (b < nt) {
+                const int u = perm ? perm[ub + b] : ub + b;
+                const int A = m2l_t[u], B = m2l_s[u];
+                batch_angles<T>(a.ang, b, lane, p, nc[A], nc[B]);
+                if (lane == 0) {
+                    h.zoff[b] = m2l_off[u];
+                    h.pin[b] = child0[B] < 0 ? q : p;
+                    h.row[b] = TR ? A : B;
+                }
+            } else if (lane == 0) {
+                h.row[b] = -1;
+                h.pin[b] = 0;
+            }
+        }
+        __syncthreads();
+        int dmax = 0;
+        for (int b = 0; b < nt; ++b) dmax = max(dmax, h.pin[b]);
+        batch_load(h, X, a.V, nbp, p, TR);
+        const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
+        batch_translate(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbp);
+        const int nd2 = (d2 + 1) * (d2 + 1);
+        for (int i = threadIdx.x; i < nd2; i += blockDim.x) {
+            T s = a.acc[i];
+            for (int b = 0; b < nt; ++b) s += a.W[(size_t)b * nbp + i];
+            a.acc[i] = s;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < nbp; i += blockDim.x) part[(size_t)ck * nbp + i] = a.acc[i];
+}
+
+// Tree passes, FMM_TB translations per CTA, nodes [first, first + count) of one level.
+//   KIND 0 (M2M):   M_k = sum over the two children c of M2M(c -> k) M_c          (4 nodes per CTA)
+//   KIND 1 (L2L):   L_k = (k's M2L chunks) + L2L(parent -> k) L_parent            (8 nodes per CTA)
+//   KIND 2 (L2L^T): Lambda_k = sum over the children c of L2L(k -> c)^T Lambda_c  (4 nodes per CTA)
+//   KIND 3 (M2M^T): Psi_k = (k's transposed M2L chunks) + M2M(k -> parent)^T Psi_parent (8 per CTA)
+// Leaves are skipped by the kinds 0 and 2 (their rows were written by the leaf kernels).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(FMM_BT) k_fmm_tree_batch(int first, int count, int p, int q, long long jpsize,
+                                                           const int* __restrict__ parent,
+                                                           const int* __restrict__ child0,
+                                                           const int* __restrict__ ck_ptr, const T* __restrict__ part,
+                                                           const long long* __restrict__ off,
+                                                           const double4* __restrict__ nc, const T* __restrict__ JPg,
+                                                           const T* __restrict__ coax, T* __restrict__ X) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nbp = (p + 1) * (p + 1);
+    const BatchHead h = batch_head(smraw);
+    const BatchArrays<T> a = batch_arrays<T>(smraw, jpsize, nbp, 0);
+    batch_setup(a, h, JPg, jpsize, p);
+    constexpr bool pairs = (KIND == 0 || KIND == 2);
+    constexpr int per = pairs ? FMM_TB / 2 : FMM_TB;     // nodes per CTA
+    constexpr bool TR = (KIND >= 2);
+    const int k0 = first + blockIdx.x * per;
+    {
+        const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int k = k0 + (pairs ? b / 2 : b);
+        int src = -1, tgt = -1;
+        long long zo = 0;
+        int pn = p;
+        if (k < first + count) {
+            if (KIND == 0) {            // child -> k
+                if (child0[k] >= 0) { src = child0[k] + (b & 1); tgt = k; zo = off[src]; pn = child0[src] < 0 ? q : p; }
+            } else if (KIND == 1) {     // parent -> k
+                if (parent[k] >= 0) { src = parent[k]; tgt = k; zo = off[k]; }
+            } else if (KIND == 2) {     // k -> child (transposed)
+                if (child0[k] >= 0) { tgt = child0[k] + (b & 1); src = k; zo = off[tgt]; }
+            } else {                    // k -> parent (transposed)
+                if (parent[k] >= 0) { src = k; tgt = parent[k]; zo = off[k]; pn = child0[k] < 0 ? q : p; }
+            }
+        }
+        if (src >= 0) batch_angles<T>(a.ang, b, lane, p, nc[tgt], nc[src]);
+        if (lane == 0) {
+            h.zoff[b] = zo;
+            h.pin[b] = pn;
+            h.row[b] = src < 0 ? -1 : (TR ? tgt : src);   // the row read: the forward input, or the transposed input
+        }
+    }
+    __syncthreads();
+    // forward inputs have degree pin (M2M) or p (L2L); transposed inputs degree p
+    for (int e = threadIdx.x; e < FMM_TB * nbp; e += blockDim.x) {
+        const int b = e / nbp, i = e - b * nbp;
+        const int rw = h.row[b];
+        const int dl = TR ? p : h.pin[b];
+        a.V[e] = (rw >= 0 && i < (dl + 1) * (dl + 1)) ? X[(size_t)rw * nbp + i] : (T)0;
+    }
+    __syncthreads();
+    int dmax = 0;
+    for (int b = 0; b < FMM_TB; ++b) dmax = max(dmax, h.pin[b]);
+    const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
+    batch_translate(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbp);
+    // combine and write (each node owned by one thread per coefficient: fixed order)
+    for (int e = threadIdx.x; e < per * nbp; e += blockDim.x) {
+        const int g = e / nbp, i = e - g * nbp;
+        const int k = k0 + g;
+        if (k >= first + count) continue;
+        if (pairs) {
+            if (child0[k] < 0) continue;
+            X[(size_t)k * nbp + i] = a.W[(size_t)(2 * g) * nbp + i] + a.W[(size_t)(2 * g + 1) * nbp + i];
+        } else {
+            T s = 0;
+            for (int ck = ck_ptr[k]; ck < ck_ptr[k + 1]; ++ck) s += part[(size_t)ck * nbp + i];
+            if (h.row[g] >= 0) s += a.W[(size_t)g * nbp + i];
+            X[(size_t)k * nbp + i] = s;
+        }
+    }
+}
+
+template <typename T>
+size_t fmm_batch_smem(int p, long long jpsize, int nacc) {
+    const int nbp = (p + 1) * (p + 1);
+    return FMM_BATCH_HEAD + sizeof(T) * ((size_t)jpsize + (2 * (size_t)FMM_TB + nacc) * nbp + FMM_TB * 4 * 32);
 }
 
 // ---------------------------------------------------------------- host
@@ -1049,7 +1118,28 @@ ddlpb_status fmm_build(ddlpb_ctx* c, const double* hc) {
         DDLPB_TRY(ctx_alloc(c, &F.l2l_off, n_nodes));
         k_fmm_coax_offsets<<<ceil_div(n_tr, 256), 256, 0, st>>>(n_m2l, n_nodes, off, F.m2l_off, F.m2m_off, F.l2l_off);
         DDLPB_LAUNCHED(c, "fmm_coax_offsets");
+        int* cnt = nullptr;
+        DDLPB_TRY(ctx_alloc(c, &cnt, 1));
+        DDLPB_CK(c, cudaMemsetAsync(cnt, 0, sizeof(int), st));
+        if (n_m2l > 0) {
+            k_fmm_count_leaf_src<<<ceil_div(n_m2l, 256), 256, 0, st>>>(n_m2l, F.m2l_s, F.child0, cnt);
+            DDLPB_LAUNCHED(c, "fmm_count_leaf_src");
+        }
+        int n_leaf_src = 0;
+        DDLPB_CK(c, cudaMemcpyAsync(&n_leaf_src, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
         DDLPB_CK(c, cudaStreamSynchronize(st));
+        // per translation: two J products at the input degree, two at the output degree, the
+        // coaxial products (m and -m), 2 flops per multiply-add
+        auto flops = [&](int pin) {
+            auto S = [](int d) { double s = 0; for (int l = 0; l <= d; ++l) s += (2.0 * l + 1) * (2.0 * l + 1); return s; };
+            double cx = 0;
+            for (int m = 0; m <= std::min(pin, p); ++m) cx += (m == 0 ? 1.0 : 2.0) * (pin + 1 - m) * (p + 1 - m);
+            return 2.0 * (2.0 * S(pin) + 2.0 * S(p) + cx);
+        };
+        c->info.fmm_nodes = n_nodes;
+        c->info.fmm_m2l = n_m2l;
+        c->info.fmm_near_pairs = n_near;
+        c->info.fmm_m2l_flops = n_leaf_src * flops(F.q) + (double)(n_m2l - n_leaf_src) * flops(p);
     }
     return DDLPB_OK;
 }
@@ -1073,9 +1163,17 @@ static ddlpb_status fmm_prepare(ddlpb_ctx* c, FmmOps<T>& O) {
     DDLPB_TRY(ctx_alloc(c, &goff, gi.off.size()));
     DDLPB_CK(c, cudaMemcpyAsync(gtab, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, st));
     DDLPB_CK(c, cudaMemcpyAsync(goff, gi.off.data(), sizeof(long long) * gi.off.size(), cudaMemcpyHostToDevice, st));
-    std::vector<T> Jt(Jh.begin(), Jh.end());
-    DDLPB_TRY(ctx_alloc(c, &O.J, Jt.size()));
-    DDLPB_CK(c, cudaMemcpyAsync(O.J, Jt.data(), sizeof(T) * Jt.size(), cudaMemcpyHostToDevice, st));
+    // J with every degree block zero-padded to n4 x n4 (n4 = 2l+1 rounded up to 4), row-major
+    std::vector<T> Jp;
+    for (int l = 0; l <= p; ++l) {
+        const int n = 2 * l + 1, n4 = (n + 3) / 4 * 4;
+        const double* Jl = Jh.data() + fmmhost::jblock(l);
+        for (int r = 0; r < n4; ++r)
+            for (int k = 0; k < n4; ++k) Jp.push_back(r < n && k < n ? (T)Jl[(size_t)r * n + k] : (T)0);
+    }
+    O.jpsize = (long long)Jp.size();
+    DDLPB_TRY(ctx_alloc(c, &O.JP, Jp.size()));
+    DDLPB_CK(c, cudaMemcpyAsync(O.JP, Jp.data(), sizeof(T) * Jp.size(), cudaMemcpyHostToDevice, st));
     DDLPB_TRY(ctx_alloc(c, &O.coax, std::max<long long>(F.coax_size, 1)));
     const int n_tr = F.n_m2l + 2 * F.n_nodes;
     k_fmm_coax<T><<<n_tr, 128, 0, st>>>(F.n_m2l, F.n_nodes, p, F.q, c->kappa, F.m2l_t, F.m2l_s, F.child0, F.parent,
@@ -1096,12 +1194,6 @@ template <typename T> static FmmOps<T>& fmm_ops(ddlpb_ctx* c);
 template <> FmmOps<double>& fmm_ops<double>(ddlpb_ctx* c) { return c->fmm64; }
 template <> FmmOps<float>& fmm_ops<float>(ddlpb_ctx* c) { return c->fmm32; }
 
-template <typename T>
-static size_t fmm_smem(const FmmTree& F) {
-    const int nbp = (F.p + 1) * (F.p + 1);
-    return sizeof(T) * ((size_t)fmmhost::jblock(F.p + 1) + (size_t)FMM_WARPS * (3 * nbp + 4 * 32));
-}
-
 template <typename T, typename K>
 static ddlpb_status fmm_smem_attr(ddlpb_ctx* c, K kernel, size_t bytes) {
     if (bytes > 48 * 1024)
@@ -1110,7 +1202,8 @@ static ddlpb_status fmm_smem_attr(ddlpb_ctx* c, K kernel, size_t bytes) {
 }
 
 // phi_ext[t] = sum_j mu_j . (k-ratio basis of sphere j)(x_t) at every external point t: far
-// field by the FMM, near pairs directly.
+// field by the FMM, near pairs directly.  Timers (kernel_timing): fmm_m2l (level 1), fmm_tree
+// (leaf multipoles, M2M and L2L passes) and fmm_near (leaf evaluation with the near pairs).
 template <typename T>
 ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     using V4 = typename FmmOps<T>::V4;
@@ -1118,33 +1211,43 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     FmmOps<T>& O = fmm_ops<T>(c);
     DDLPB_TRY(fmm_prepare<T>(c, O));
     const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax;
-    const long long js = fmmhost::jblock(p + 1);
     cudaStream_t st = c->stream;
-    const size_t sm = fmm_smem<T>(F);
-    KernelTimer kt(c, "fmm_pot", sizeof(T) == 4);
-    k_fmm_leaf_mult<T><<<M, 128, 0, st>>>(M, c->nb, nbp, F.leaf_node, mu, O.Mx);
-    DDLPB_LAUNCHED(c, "fmm_leaf_mult");
-    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2m<T, V4>, sm)));
-    for (int lv = F.depth - 1; lv >= 0; --lv) {
-        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
-        k_fmm_m2m<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(first, count, p, q, js, F.child0,
-                                                                                F.m2m_off, F.node_g, O.J, O.coax, O.Mx);
-        DDLPB_LAUNCHED(c, "fmm_m2m");
+    const bool f32 = sizeof(T) == 4;
+    const size_t sm0 = fmm_batch_smem<T>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T>(p, O.jpsize, 1);
+    {
+        KernelTimer kt(c, "fmm_tree", f32, 2);
+        k_fmm_leaf_mult<T><<<M, 128, 0, st>>>(M, c->nb, nbp, F.leaf_node, mu, O.Mx);
+        DDLPB_LAUNCHED(c, "fmm_leaf_mult");
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_tree_batch<T, 0>, sm0)));
+        for (int lv = F.depth - 1; lv >= 0; --lv) {
+            const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+            k_fmm_tree_batch<T, 0><<<ceil_div(count, FMM_TB / 2), FMM_BT, sm0, st>>>(
+                first, count, p, q, O.jpsize, F.parent, F.child0, nullptr, nullptr, F.m2m_off, F.node_g, O.JP, O.coax,
+                O.Mx);
+            DDLPB_LAUNCHED(c, "fmm_m2m");
+        }
     }
     if (F.n_ck > 0) {
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l<T, V4>, sm)));
-        k_fmm_m2l<T, V4><<<ceil_div(F.n_ck, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
-            F.n_ck, p, q, js, F.ck_b, F.ck_e, F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.J, O.coax, O.Mx, O.part);
+        KernelTimer kt(c, "fmm_m2l", f32);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, false>, sm1)));
+        k_fmm_m2l_batch<T, false><<<F.n_ck, FMM_BT, sm1, st>>>(F.n_ck, p, q, O.jpsize, F.ck_b, F.ck_e, nullptr, F.m2l_t,
+                                                                F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP, O.coax,
+                                                                O.Mx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l");
     }
-    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_l2l<T, V4>, sm)));
-    for (int lv = 0; lv <= F.depth; ++lv) {
-        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
-        k_fmm_l2l<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
-            first, count, p, js, F.parent, F.tck_ptr, O.part, F.l2l_off, F.node_g, O.J, O.coax, O.Lx);
-        DDLPB_LAUNCHED(c, "fmm_l2l");
+    {
+        KernelTimer kt(c, "fmm_tree", f32, 2);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_tree_batch<T, 1>, sm0)));
+        for (int lv = 0; lv <= F.depth; ++lv) {
+            const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+            k_fmm_tree_batch<T, 1><<<ceil_div(count, FMM_TB), FMM_BT, sm0, st>>>(
+                first, count, p, q, O.jpsize, F.parent, F.child0, F.tck_ptr, O.part, F.l2l_off, F.node_g, O.JP, O.coax,
+                O.Lx);
+            DDLPB_LAUNCHED(c, "fmm_l2l");
+        }
     }
     if (c->E > 0) {
+        KernelTimer kt(c, "fmm_near", f32, 2);
         const size_t sm2 = sizeof(T) * ((size_t)nbp + (size_t)(L + 1) * 128);
         DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_pot<T, V4>, sm2)));
         k_fmm_leaf_pot<T, V4><<<M, 128, sm2, st>>>(c->N, c->nb, L, p, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph,
@@ -1157,49 +1260,60 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
 
 // nu_j = sum_t c_t (k-ratio basis of sphere j)(x_t) over the external points (the transpose of
 // fmm_potential); the far part of sphere j's adjoint to degree q is kept in FmmOps::leafq.
+// Timers: fmm_m2l_T (level 1), fmm_tree, fmm_near.
 template <typename T>
 ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
     using V4 = typename FmmOps<T>::V4;
     FmmTree& F = c->fmm;
     FmmOps<T>& O = fmm_ops<T>(c);
     DDLPB_TRY(fmm_prepare<T>(c, O));
-    const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax, N = c->N;
-    const long long js = fmmhost::jblock(p + 1);
+    const int p = F.p, q = F.q, M = c->M, L = c->lmax, N = c->N;
     cudaStream_t st = c->stream;
-    const size_t sm = fmm_smem<T>(F);
-    KernelTimer kt(c, "fmm_adj", sizeof(T) == 4);
-    const size_t sm0 = (sizeof(T) + sizeof(int)) * (size_t)N;
-    k_fmm_leaf_lambda<T><<<M, 128, sm0, st>>>(N, p, c->ext_ptr, c->ext_p, F.leaf_node, O.Yp, c_ext, O.Lx);
-    DDLPB_LAUNCHED(c, "fmm_leaf_lambda");
-    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_l2l_T<T, V4>, sm)));
-    for (int lv = F.depth - 1; lv >= 0; --lv) {
-        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
-        k_fmm_l2l_T<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(first, count, p, js, F.child0,
-                                                                                  F.l2l_off, F.node_g, O.J, O.coax,
-                                                                                  O.Lx);
-        DDLPB_LAUNCHED(c, "fmm_l2l_T");
+    const bool f32 = sizeof(T) == 4;
+    const size_t sm0 = fmm_batch_smem<T>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T>(p, O.jpsize, 1);
+    {
+        KernelTimer kt(c, "fmm_tree", f32, 2);
+        const size_t smL = (sizeof(T) + sizeof(int)) * (size_t)N;
+        k_fmm_leaf_lambda<T><<<M, 128, smL, st>>>(N, p, c->ext_ptr, c->ext_p, F.leaf_node, O.Yp, c_ext, O.Lx);
+        DDLPB_LAUNCHED(c, "fmm_leaf_lambda");
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_tree_batch<T, 2>, sm0)));
+        for (int lv = F.depth - 1; lv >= 0; --lv) {
+            const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+            k_fmm_tree_batch<T, 2><<<ceil_div(count, FMM_TB / 2), FMM_BT, sm0, st>>>(
+                first, count, p, q, O.jpsize, F.parent, F.child0, nullptr, nullptr, F.l2l_off, F.node_g, O.JP, O.coax,
+                O.Lx);
+            DDLPB_LAUNCHED(c, "fmm_l2l_T");
+        }
     }
     if (F.n_ckT > 0) {
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_T<T, V4>, sm)));
-        k_fmm_m2l_T<T, V4><<<ceil_div(F.n_ckT, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
-            F.n_ckT, p, q, js, F.ckT_b, F.ckT_e, F.m2lT_k, F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.J,
-            O.coax, O.Lx, O.part);
+        KernelTimer kt(c, "fmm_m2l_T", f32);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, true>, sm1)));
+        k_fmm_m2l_batch<T, true><<<F.n_ckT, FMM_BT, sm1, st>>>(F.n_ckT, p, q, O.jpsize, F.ckT_b, F.ckT_e, F.m2lT_k,
+                                                                F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP,
+                                                                O.coax, O.Lx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l_T");
     }
-    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2m_T<T, V4>, sm)));
-    for (int lv = 0; lv <= F.depth; ++lv) {
-        const int first = F.lev[lv], count = F.lev[lv + 1] - first;
-        k_fmm_m2m_T<T, V4><<<ceil_div(count, FMM_WARPS), 32 * FMM_WARPS, sm, st>>>(
-            first, count, p, q, js, F.parent, F.child0, F.sck_ptr, O.part, F.m2m_off, F.node_g, O.J, O.coax, O.Mx);
-        DDLPB_LAUNCHED(c, "fmm_m2m_T");
+    {
+        KernelTimer kt(c, "fmm_tree", f32, 2);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_tree_batch<T, 3>, sm0)));
+        for (int lv = 0; lv <= F.depth; ++lv) {
+            const int first = F.lev[lv], count = F.lev[lv + 1] - first;
+            k_fmm_tree_batch<T, 3><<<ceil_div(count, FMM_TB), FMM_BT, sm0, st>>>(
+                first, count, p, q, O.jpsize, F.parent, F.child0, F.sck_ptr, O.part, F.m2m_off, F.node_g, O.JP, O.coax,
+                O.Mx);
+            DDLPB_LAUNCHED(c, "fmm_m2m_T");
+        }
     }
-    const int nw = 128 / 32;
-    const size_t sm3 = sizeof(T) * ((size_t)nw * c->nb + (L + 2) + (size_t)(L + 1) * 128);
-    DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_adj<T, V4>, sm3)));
-    k_fmm_leaf_adj<T, V4><<<M, 128, sm3, st>>>(N, c->nb, L, p, q, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph, c->leb,
-                                               F.leaf_node, O.Mx, F.nearT_ptr, F.nearT_i, c_ext, S.Khinv, S.yt, nu,
-                                               O.leafq);
-    DDLPB_LAUNCHED(c, "fmm_leaf_adj");
+    {
+        KernelTimer kt(c, "fmm_near", f32, 2);
+        const int nw = 128 / 32;
+        const size_t sm3 = sizeof(T) * ((size_t)nw * c->nb + (L + 2) + (size_t)(L + 1) * 128);
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_adj<T, V4>, sm3)));
+        k_fmm_leaf_adj<T, V4><<<M, 128, sm3, st>>>(N, c->nb, L, p, q, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph,
+                                                   c->leb, F.leaf_node, O.Mx, F.nearT_ptr, F.nearT_i, c_ext, S.Khinv,
+                                                   S.yt, nu, O.leafq);
+        DDLPB_LAUNCHED(c, "fmm_leaf_adj");
+    }
     return DDLPB_OK;
 }
 
@@ -1418,3 +1532,4 @@ ddlpb_status fmm_force_terms(ddlpb_ctx* c, const double* mu, const double4* fs, 
     DDLPB_LAUNCHED(c, "fmm_force_sources");
     return DDLPB_OK;
 }
+

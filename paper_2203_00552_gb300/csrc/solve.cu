@@ -573,7 +573,7 @@ static ddlpb_status setup_common(int n, const double* centres, const double* rad
     if (o.gmres_restart < 1 || o.gmres_restart > 2000) return fail("gmres_restart must be in [1, 2000]");
     if (o.precision != DDLPB_FP64 && o.precision != DDLPB_MIXED) return fail("unknown precision");
     if (o.fmm_order != 0 && (o.fmm_order < lmax + 1 || o.fmm_order > DDLPB_FMM_PMAX))
-        return fail("fmm_order must be 0 (direct summation) or in [lmax + 1, 22]");
+        return fail("fmm_order must be 0 (direct summation) or in [lmax + 1, 21]");
     if (o.fmm_order != 0 && !(o.fmm_theta > 0.0 && o.fmm_theta < 1.0)) return fail("fmm_theta must be in (0, 1)");
     if (!(o.precond_tol > 0.0 && o.precond_tol <= 1.0)) return fail("precond_tol must be in (0, 1]");
     ddlpb_ctx* c = new ddlpb_ctx();
