@@ -280,3 +280,62 @@ def test_kirkwood_tanford_off_centre_charge(lmax, n):
     # the l > 0 terms matter: dropping them changes the energy well beyond the tolerance
     E0, _ = _kirkwood_tanford(0.7, a, b, eps2, kap, 0)
     assert abs(E_ref - E0) > 1e-4 * abs(E_ref)
+
+
+# ---------------------------------------------------------------- A and B entry by entry
+# Eqs. definition_of_A_matrix, definition_of_B_matrix with the switch weights of Eqs.
+# regular_omega_ij, di, regular_chi_e: sum_j omega_ij^eta = 1 - chi_i^eta at every grid point
+# (d^i = min(f, 1)/f), and each neighbour's expansion of a harmonic polynomial (basis r_l Y) or
+# of a plane wave exp(kappa u.x) (basis i-ratio Y, an exact solution of the screened equation)
+# is exact, so (A X_h)_i = analysis_i(chi_i h) and (B X_pw)_i = analysis_i(chi_i pw) sphere by
+# sphere.  A wrong omega (e.g. d = 1/f also where f < 1), a wrong radial scaling or a wrong
+# Y_lm convention breaks these identities on any geometry with partly covered spheres.
+
+def _dense_globule(lmax=4, n=50):
+    c, r, q = synth.molecule(14, 2, "eden", None, "vdw")
+    P = O.DDLPB(c, r, q, 78.54, KAPPA, lmax, n)
+    f = P.f
+    # the geometry must reach both branches of d^i and partial covering
+    assert (f > 1.0).any() and ((f > 0.0) & (f < 1.0)).any()
+    return P
+
+
+def harmonic_expansions(P, centre, L, M):
+    """Coefficients about every sphere of the solid harmonic R_LM(x - centre) (degree L <= lmax)
+    in the basis (rho/r_j)^l Y_lm, from its values on each sphere (exact: a polynomial of degree
+    <= lmax)."""
+    vals = np.stack([sph.solid_harmonics(L, P.pts[j] - centre)[:, L * L + L + M] for j in range(P.M)])
+    return vals, np.stack([P.analysis(vals[j]) for j in range(P.M)])
+
+
+@pytest.mark.parametrize("L,M", [(0, 0), (1, -1), (2, 1), (3, 0), (4, -3)])
+def test_A_reproduces_harmonic_polynomials(L, M):
+    P = _dense_globule()
+    vals, X = harmonic_expansions(P, np.array([0.7, -1.3, 2.1]), L, M)
+    lhs = P.apply_A(X)
+    rhs = np.stack([P.analysis(P.chi[i] * vals[i]) for i in range(P.M)])
+    assert np.abs(lhs - rhs).max() <= 1e-12 * max(np.abs(X).max(), 1.0)
+
+
+def plane_wave_expansions(P, u):
+    """exp(kappa u.x) about every sphere in the basis i_l(kappa rho)/i_l(kappa r_j) Y_lm:
+    X_j,lm = exp(kappa u.x_j) 4 pi i_l(kappa r_j) Y_lm(u) (the plane-wave expansion), and its
+    values at every grid point."""
+    Yu = sph.ylm(P.lmax, u[None, :])[0]
+    X = np.stack([np.exp(P.kappa * u @ P.x[j]) * 4 * np.pi * P.lexpand(P.i_r[j]) * Yu for j in range(P.M)])
+    vals = np.exp(P.kappa * P.pts @ u)
+    return vals, X
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_B_reproduces_plane_waves(seed):
+    P = _dense_globule(8, 110)
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    vals, X = plane_wave_expansions(P, u)
+    lhs = P.apply_B(X)
+    rhs = np.stack([P.analysis(P.chi[i] * vals[i]) for i in range(P.M)])
+    # truncation at lmax = 8 of the plane wave: about (kappa rho)^9 / 19!! with kappa rho < 0.35,
+    # below 1e-12 (at lmax = 4 it is 1e-7)
+    assert np.abs(lhs - rhs).max() <= 1e-11 * np.abs(X).max()
