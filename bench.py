@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fmm-order", type=int, default=None,
                     help="FMM expansion order (default: the workload's; 0 = direct summation)")
+    ap.add_argument("--fmm-theta", type=float, default=0.4,
+                    help="FMM admissibility ratio: M2L when Rt_A + Rs_B < theta |c_A - c_B|")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing (profiling runs)")
     ap.add_argument("--no-breakdown", action="store_true", help="skip the instrumented breakdown step")
@@ -233,7 +235,7 @@ def main():
     prec = G.DDLPB_MIXED if args.precision == "mixed" else G.DDLPB_FP64
     fmm_order = w["fmm_order"] if args.fmm_order is None else args.fmm_order
     opts = dict(tol=1e-8, precision=prec, gmres_restart=args.restart, precond_tol=args.precond_tol, max_iter=4000,
-                fmm_order=fmm_order)
+                fmm_order=fmm_order, fmm_theta=args.fmm_theta)
     M = w["n"]
     cen = torch.tensor(w["centres"], device=dev)
     rad = torch.tensor(w["radii"], device=dev)
@@ -420,7 +422,7 @@ def main():
                 "config": {"workload": args.workload, "atoms": M, "lmax": w["lmax"], "n_lebedev": w["n_lebedev"],
                            "surface": w["surface"], "precision": args.precision,
                            "coupling": ("fmm" if fmm_order > 0 else "direct summation"), "fmm_order": fmm_order,
-                           "fmm_theta": 0.5 if fmm_order > 0 else None,
+                           "fmm_theta": opts["fmm_theta"] if fmm_order > 0 else None,
                            "tol": 1e-8, "gmres_restart": args.restart, "precond_tol": args.precond_tol,
                            "l2": "512 MB buffer written between timed steps; working set > L2",
                            "parallelism": "replicas" if world > 1 else "single"},

@@ -87,7 +87,10 @@ typedef struct {
                             arithmetic; an inexact preconditioner is allowed in flexible GMRES);
                             0: they use the FP32 basis; no effect in the FP64 form; default 1 */
     double fmm_theta;    /* admissibility of the FMM: a target node A and source node B interact by
-                            M2L when Rt_A + Rs_B < fmm_theta |c_A - c_B|; in (0, 1); default 0.5 */
+                            M2L when Rt_A + Rs_B < fmm_theta |c_A - c_B|; in (0, 1); default 0.4
+                            (the far-field error falls steeply with it: at order 16 on a
+                            1000-sphere SAS globule, lmax 8, the energy error against direct
+                            summation is 9e-5 at 0.5, 5e-8 at 0.4, 1.5e-10 at 0.3) */
 } ddlpb_options;
 
 typedef struct {

@@ -110,7 +110,7 @@ class DDLPB:
     """
 
     def __init__(self, centres, radii, charges, eps_solvent, kappa, lmax, n_lebedev,
-                 surface="vdw", eta=0.1, eps_solute=1.0, fmm_order=0):
+                 surface="vdw", eta=0.1, eps_solute=1.0, fmm_order=0, fmm_theta=0.4):
         self.x = np.array(centres, dtype=np.float64).reshape(-1, 3)
         r = np.array(radii, dtype=np.float64).reshape(-1)
         if surface == "sas":
@@ -127,6 +127,7 @@ class DDLPB:
         self.nb = sph.nbasis(lmax)
         self.eta = float(eta)
         self.fmm_order = int(fmm_order)   # > 0: Yukawa far field by the tree of oracle/fmm.py
+        self.fmm_theta = float(fmm_theta)  # admissibility ratio of that tree
         self._tree = None
         self.s, self.w, self.degree = sph.lebedev(n_lebedev)
         self.N = self.s.shape[0]
@@ -208,19 +209,24 @@ class DDLPB:
         (Eqs. derivative_ylm, derivative_radial, derivative_bessel,
         Derivative_of_k_l0 for the k = i case).
         """
-        d = P - self.x[j]
+        xj, rj = self.x[j], self.r[j]
+        i_r, k_r = self.i_r[j], self.k_r[j]
+        if np.ndim(j) == 1:   # several spheres at once: results [len(j), ..., nb]
+            xj, rj = xj[:, None, :], rj[:, None, None]
+            i_r, k_r = i_r[:, None, :], k_r[:, None, :]
+        d = P - xj
         rho = np.linalg.norm(d, axis=-1)
         e = d / rho[..., None]
         ls = np.arange(self.lmax + 1)
         if kind == "r":
-            R = (rho[..., None] / self.r[j]) ** ls
-            dR = ls * (rho[..., None] / self.r[j]) ** np.maximum(ls - 1, 0) / self.r[j]
+            R = (rho[..., None] / rj) ** ls
+            dR = ls * (rho[..., None] / rj) ** np.maximum(ls - 1, 0) / rj
         elif kind == "i":
-            R = sph.bessel_i(ls, self.kappa * rho[..., None]) / self.i_r[j]
-            dR = self.kappa * sph.bessel_i_deriv(ls, self.kappa * rho[..., None]) / self.i_r[j]
+            R = sph.bessel_i(ls, self.kappa * rho[..., None]) / i_r
+            dR = self.kappa * sph.bessel_i_deriv(ls, self.kappa * rho[..., None]) / i_r
         elif kind == "k":
-            R = sph.bessel_k(ls, self.kappa * rho[..., None]) / self.k_r[j]
-            dR = self.kappa * sph.bessel_k_deriv(ls, self.kappa * rho[..., None]) / self.k_r[j]
+            R = sph.bessel_k(ls, self.kappa * rho[..., None]) / k_r
+            dR = self.kappa * sph.bessel_k_deriv(ls, self.kappa * rho[..., None]) / k_r
         else:
             raise ValueError(kind)
         R = self.lexpand(R)
@@ -263,19 +269,19 @@ class DDLPB:
         return np.array(out)
 
     def apply_K_rows(self, y, rows):
-        """Rows `rows` of apply_K(y) (all sources, sampled targets)."""
-        src = [j for j in range(self.M) if np.any(self.chi[j] > 0)]
-        mu = np.zeros((self.M, self.nb))
-        for j in src:   # P chi_j = 0 on spheres without external points
-            mu[j] = self.lexpand(self.cik[j]) * (self._pchi(j) @ y[j])
+        """Rows `rows` of apply_K(y) (all sources, sampled targets).  P chi_j y_j is formed as
+        analysis(chi_j synthesis(y_j)), the same product as [P chi_j] y_j."""
+        src = np.array([j for j in range(self.M) if np.any(self.chi[j] > 0)])
+        mu = self.lexpand(self.cik) * self.analysis(self.chi * self.synthesis(y))
         out = []
         for i in rows:
             ext = self.chi[i] > 0
             phi = np.zeros(self.N)
             if ext.any():
                 P = self.pts[i][ext]
-                for j in src:
-                    phi[ext] += self.basis("k", j, P) @ mu[j]
+                for s in range(0, len(src), 128):   # sources in blocks
+                    js = src[s:s + 128]
+                    phi[ext] += np.einsum("jpn,jn->p", self.basis("k", js, P), mu[js])
             out.append(self.analysis(self.chi[i] * phi))
         return np.array(out)
 
@@ -291,6 +297,34 @@ class DDLPB:
                 out[j] -= (self.omega(i, j) * zi) @ self.basis(kind, j, self.pts[i])
         return out
 
+    def apply_AT_rows(self, Yc, rows, kind="r"):
+        """Rows `rows` of A^T Y (kind 'r') or B^T Y (kind 'i'): row j collects the entries A_ij
+        over the spheres i that overlap j (the overlap relation is symmetric)."""
+        out = []
+        for j in rows:
+            acc = Yc[j].copy()
+            for i in self.nbrs[j]:
+                zi = self.w * self.synthesis(Yc[i])
+                acc -= (self.omega(i, j) * zi) @ self.basis(kind, j, self.pts[i])
+            out.append(acc)
+        return np.array(out)
+
+    def apply_KT_rows(self, lam, rows):
+        """Rows `rows` of apply_KT(lam), every target sphere summed directly."""
+        z = self.w * self.chi * self.synthesis(lam)      # [M, N]
+        ext = self.chi > 0
+        P, zf = self.pts[ext], z[ext]                     # every point with chi > 0
+        out = []
+        for j in rows:
+            nu = np.zeros(self.nb)
+            if not ext[j].any():          # P chi_j = 0: the row vanishes
+                out.append(nu)
+                continue
+            for s in range(0, len(P), 65536):
+                nu += zf[s:s + 65536] @ self.basis("k", j, P[s:s + 65536])
+            out.append(self._pchi(j) @ (self.lexpand(self.cik[j]) * nu))
+        return np.array(out)
+
     def _pchi(self, j):
         """[P chi_j^e] (Eq. definition_of_P_matrix), nb x nb."""
         return (self.Y * (self.w * self.chi[j])[:, None]).T @ self.Y
@@ -304,7 +338,7 @@ class DDLPB:
     def _fmm(self):
         if self._tree is None:
             from .fmm import YukawaFMM
-            self._tree = YukawaFMM(self.x, self.r, self.kappa, self.lmax, self.fmm_order)
+            self._tree = YukawaFMM(self.x, self.r, self.kappa, self.lmax, self.fmm_order, self.fmm_theta)
             self._ext = [np.nonzero(self.chi[i] > 0)[0] for i in range(self.M)]
             self._Yp = sph.ylm(self.fmm_order, self.s)                 # [N, (p+1)^2]
             # near sources of each target sphere, and the near targets of each source sphere

@@ -26,7 +26,7 @@ GPU path shares:
     a leaf's multipole is the sphere's mu_j itself (degree lmax, scale r_j), and a leaf's local
     evaluated on its own sphere is sum L_lm Y_lm(s_n);
   * dual traversal from (root, root): (A target, B source) is admissible when
-    Rt_A + Rs_B < theta |c_A - c_B| (theta = 1/2): one M2L; else two leaves: near pair, summed
+    Rt_A + Rs_B < theta |c_A - c_B| (default theta = 0.4): one M2L; else two leaves: near pair, summed
     directly; else split A if B is a leaf or (A is not a leaf and Rt_A >= Rs_B), otherwise B.
 Translations here are computed by projection: the source expansion is evaluated on a sphere of
 radius rho about the new centre and projected onto Y_lm with a Gauss-Legendre x trapezoid rule
@@ -112,7 +112,7 @@ class YukawaFMM:
     p (expansion order, >= lmax), theta.
     """
 
-    def __init__(self, centres, radii, kappa, lmax, p, theta=0.5):
+    def __init__(self, centres, radii, kappa, lmax, p, theta=0.4):
         if p < lmax:
             raise ValueError("the expansion order must be at least lmax")
         self.x = np.asarray(centres, dtype=float).reshape(-1, 3)

@@ -100,7 +100,7 @@ struct OpSet {
 struct FmmTree {
     bool on = false;
     int p = 0, q = 0;                 // expansion order; degree of the leaf multipoles (min(p, lmax + 1))
-    double theta = 0.5;
+    double theta = 0.4;
     int n_nodes = 0, depth = 0;
     std::vector<int> lev;             // host: first node of each level, lev[depth + 1] = n_nodes
     std::vector<int> host_child0;     // host copy of child0 (internal nodes per level)

@@ -542,7 +542,7 @@ extern "C" void ddlpb_default_options(ddlpb_options* o) {
     o->kernel_timing = 0;
     o->precond_coupling = 0;
     o->precond_fp16 = 1;
-    o->fmm_theta = 0.5;
+    o->fmm_theta = 0.4;
 }
 
 static ddlpb_status setup_common(int n, const double* centres, const double* radii, const double* charges,

@@ -34,7 +34,7 @@ def test_tree_covers_every_pair_once_and_respects_admissibility(globule24):
     cover = np.zeros((M, M), dtype=int)
     for A, B in F.m2l:
         d = np.linalg.norm(F.c[A] - F.c[B])
-        assert F.Rt[A] + F.Rs[B] < 0.5 * d
+        assert F.Rt[A] + F.Rs[B] < F.theta * d
         for i in _leaves_below(F, A):
             for j in _leaves_below(F, B):
                 cover[i, j] += 1
@@ -42,7 +42,7 @@ def test_tree_covers_every_pair_once_and_respects_admissibility(globule24):
         for j in F.near[i]:
             cover[i, j] += 1
             d = np.linalg.norm(c[i] - c[j])
-            assert not (r[i] < 0.5 * d)          # a near pair of leaves is not admissible
+            assert not (r[i] < F.theta * d)      # a near pair of leaves is not admissible
     assert (cover == 1).all()
     # node geometry: every sphere of a node lies within Rs of its centre, its ball within Rt
     for k in range(len(F.a)):

@@ -17,6 +17,8 @@ from oracle import ddlpb as O
 from oracle import sph
 from paper_2203_00552_gb300 import synth
 
+from expansions import harmonic_expansions, plane_wave_expansions
+
 A2B = synth.ANGSTROM_TO_BOHR
 KAPPA = 0.104 / A2B
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -192,6 +194,24 @@ def test_dense_equals_matrix_free_and_transpose(chain8):
     assert abs(L - L.T).max() > 1e-3
 
 
+def test_sampled_rows_equal_the_full_products():
+    """The sampled-row forms used at full size (rows of A X, B X, A^T Y, B^T Y and of the coupling
+    and its transpose, summed over sources in blocks) equal the rows of the full products above,
+    on a globule with buried, partly covered and exposed spheres."""
+    c, r, q = synth.molecule(30, 3, "globule", None, "sas")
+    p = O.DDLPB(c, r, q, 78.54, KAPPA, 4, 50, surface="sas")
+    n_ext = (p.chi > 0).sum(axis=1)
+    rows = [int(n_ext.argmin()), int(n_ext.argmax()), int(np.abs(n_ext - p.N // 2).argmin()), p.M - 1]
+    assert n_ext[rows[0]] == 0 and n_ext[rows[1]] > 0
+    rng = np.random.default_rng(4)
+    Y = rng.normal(size=(p.M, p.nb))
+    for kind in "ri":
+        assert np.abs(p.apply_A_rows(Y, rows, kind) - p.apply_A(Y, kind)[rows]).max() < 1e-13
+        assert np.abs(p.apply_AT_rows(Y, rows, kind) - p.apply_AT(Y, kind)[rows]).max() < 1e-13
+    for got, want in ((p.apply_K_rows(Y, rows), p.apply_K(Y)[rows]), (p.apply_KT_rows(Y, rows), p.apply_KT(Y)[rows])):
+        assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
 def test_gmres_matches_dense(chain8):
     c, r, q = chain8
     p1 = O.DDLPB(c, r, q, 78.54, KAPPA, 3, 50)
@@ -300,14 +320,6 @@ def _dense_globule(lmax=4, n=50):
     return P
 
 
-def harmonic_expansions(P, centre, L, M):
-    """Coefficients about every sphere of the solid harmonic R_LM(x - centre) (degree L <= lmax)
-    in the basis (rho/r_j)^l Y_lm, from its values on each sphere (exact: a polynomial of degree
-    <= lmax)."""
-    vals = np.stack([sph.solid_harmonics(L, P.pts[j] - centre)[:, L * L + L + M] for j in range(P.M)])
-    return vals, np.stack([P.analysis(vals[j]) for j in range(P.M)])
-
-
 @pytest.mark.parametrize("L,M", [(0, 0), (1, -1), (2, 1), (3, 0), (4, -3)])
 def test_A_reproduces_harmonic_polynomials(L, M):
     P = _dense_globule()
@@ -315,16 +327,6 @@ def test_A_reproduces_harmonic_polynomials(L, M):
     lhs = P.apply_A(X)
     rhs = np.stack([P.analysis(P.chi[i] * vals[i]) for i in range(P.M)])
     assert np.abs(lhs - rhs).max() <= 1e-12 * max(np.abs(X).max(), 1.0)
-
-
-def plane_wave_expansions(P, u):
-    """exp(kappa u.x) about every sphere in the basis i_l(kappa rho)/i_l(kappa r_j) Y_lm:
-    X_j,lm = exp(kappa u.x_j) 4 pi i_l(kappa r_j) Y_lm(u) (the plane-wave expansion), and its
-    values at every grid point."""
-    Yu = sph.ylm(P.lmax, u[None, :])[0]
-    X = np.stack([np.exp(P.kappa * u @ P.x[j]) * 4 * np.pi * P.lexpand(P.i_r[j]) * Yu for j in range(P.M)])
-    vals = np.exp(P.kappa * P.pts @ u)
-    return vals, X
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

@@ -123,6 +123,19 @@ def test_served_results_match_solo_runs():
             assert abs(ew - e) <= 1e-6 * abs(e)
             assert np.linalg.norm(fw - f) <= 1e-5 * np.linalg.norm(f)
     torch.cuda.synchronize()
+    # the smallest fresh request served in the mix against the oracle (direct coupling, solved
+    # to 1e-13): the mixed form's 1e-8 tolerance bounds both differences
+    from oracle import ddlpb as O
+    from paper_2203_00552_gb300 import synth
+    k = min((i for i, q in enumerate(reqs) if q.parent is None), key=lambda i: reqs[i].atoms)
+    q = reqs[k]
+    P = O.DDLPB(q.centres, q.radii, q.charges, synth.EPS_SOLVENT, synth.KAPPA_PER_ANGSTROM / synth.ANGSTROM_TO_BOHR,
+                q.lmax, q.n_lebedev)
+    P.solve()
+    P.adjoint()
+    E0, F0 = P.energy(), P.forces()
+    assert abs(res[k].energy - E0) <= 1e-6 * abs(E0), (res[k].energy, E0)
+    assert np.linalg.norm(res[k].forces - F0) <= 1e-5 * np.linalg.norm(F0)
 
 
 def test_sweep_degree_table_matches_the_stored_rules():
