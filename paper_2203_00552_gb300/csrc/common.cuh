@@ -146,6 +146,7 @@ struct FmmOps {
     T* coax = nullptr;        // [coax_size] coaxial translation blocks
     T* JP = nullptr;          // rotation about x by -90 degrees, degree blocks padded to multiples of 4
     long long jpsize = 0;
+    int* btab = nullptr;      // integer tables of the batched translations (degree offsets, work items)
     T* Yp = nullptr;          // [N][(p+1)^2] Y_lm(s_n), l <= p
     T* Mx = nullptr;          // [n_nodes][(p+1)^2] multipoles (transposed pass: their adjoints)
     T* Lx = nullptr;          // [n_nodes][(p+1)^2] locals (transposed pass: their adjoints)

@@ -26,8 +26,8 @@
 //   M2M: (-1)^(l+a) sum_j g i_b(kappa t)  k_a(kappa Rt_T) / k_l(kappa Rt_S)
 //   L2L:            sum_j g i_b(kappa t)  i_a(kappa Rt_T) / i_l(kappa Rt_S)
 // They are evaluated once per translation at setup in FP64 and stored in the precision of the
-// operator set (HBM holds them easily); the rotations are applied on the fly by one warp per
-// translation, with J in shared memory.
+// operator set (HBM holds them easily); the rotations are applied on the fly, a batch of
+// translations per CTA, with J in shared memory.
 //
 // Every pass gathers (one warp per target or per chunk of a target's list, partial sums added
 // in a fixed order), so the operator is deterministic: the mixed-precision refinement evaluates
@@ -479,123 +479,188 @@ __global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, cons
 
 // ---------------------------------------------------------------- batched translations
 //
-// A CTA translates FMM_TB expansions at a time.  Every rotation about x by -90 degrees is then
-// a small matrix product J_l [n x n] x [n x FMM_TB] per degree l, tiled 4 rows x 4 translations
-// per thread (each J entry read from shared memory serves 4 translations, each coefficient 4
-// rows).  J sits in shared memory with every degree block zero-padded to n4 x n4 (n4 = n rounded
-// up to 4), row-major, so that the 4 rows of a tile of J^T are one contiguous load.  The coaxial
-// step reads each translation's stored block once (consecutive threads on consecutive output
-// degrees), one load serving +m and -m.  Used by the M2L chunks (FP32 and FP64) and by the tree
-// passes (M2M, L2L and their transposes, a few nodes per CTA).
+// A CTA translates TB expansions at a time (TB = 16 for the FP32 M2L chunks, 8 otherwise).  In
+// shared memory an expansion is kept in a padded layout: degree l occupies n4 = 2l+1 rounded up
+// to 4 slots from poff[l] (a multiple of 4), the padding held at zero, so that four consecutive
+// coefficients are one vector load.  The rotation about x by -90 degrees (J) sits in shared
+// memory with every degree block zero-padded to n4 x n4, row-major.  Only products with J^T are
+// formed: J^T = S J S with S = diag(-1 for m < 0), because the reflection y -> -y maps Y_lm to
+// S Y_lm and turns the rotation about x by an angle into the rotation by minus that angle; so a
+// product with J is S J^T S, and both S are folded into the neighbouring steps.  A product
+// J^T [n x n] x [n x TB] per degree is tiled 4 rows x 4 translations per item: per four input
+// coefficients, four vector loads of J (rows k..k+3 at the item's four columns, consecutive
+// items on consecutive columns) and four of the inputs (one per translation, the same address
+// across the items of a degree) feed 64 multiply-adds.  An item's cost grows with its degree, so
+// when there are more items than threads each thread takes row groups s and R-1-s of one
+// translation group.  The coaxial step reads each translation's stored block once (8 loads in
+// flight), one load serving +m and -m.  Used by the M2L chunks and by the tree passes.
 
-#define FMM_TB 8          // translations in shared memory at a time
-#define FMM_BT 256        // threads of a batched CTA
-// shared-memory head of a batched CTA: per translation the block offset (long long), input
-// degree, source row, valid flag (int); degree tables (int); rounded up to 16 bytes
-#define FMM_BATCH_HEAD ((8 * FMM_TB + 4 * (3 * FMM_TB + 3 * (DDLPB_FMM_PMAX + 4)) + 15) / 16 * 16)
+#define FMM_TB 8           // translations per batch (tree passes, FP64 M2L)
+#define FMM_TB_M2L32 16    // translations per batch of the FP32 M2L chunks
+#define FMM_BT 256         // threads of a batched CTA
+#define FMM_RG_MAX 140     // row groups of 4 up to degree DDLPB_FMM_PMAX (132 at 21)
+#define FMM_OM_MAX 256     // (m, o) items of the coaxial step, (p+1)(p+2)/2 (253 at 21)
+// integer tables of a batched CTA (built on the host, copied to shared memory)
+#define FMM_BTAB_RGOFF 0
+#define FMM_BTAB_JPOFF (DDLPB_FMM_PMAX + 4)
+#define FMM_BTAB_POFF (2 * (DDLPB_FMM_PMAX + 4))
+#define FMM_BTAB_RGL (3 * (DDLPB_FMM_PMAX + 4))
+#define FMM_BTAB_RGR0 (FMM_BTAB_RGL + FMM_RG_MAX)
+#define FMM_BTAB_OMM (FMM_BTAB_RGR0 + FMM_RG_MAX)
+#define FMM_BTAB_OMO (FMM_BTAB_OMM + FMM_OM_MAX)
+#define FMM_BTAB (FMM_BTAB_OMO + FMM_OM_MAX)
+
+// shared-memory head: per translation the block offset (long long), input degree and source
+// row (int), then the integer tables; rounded up to 16 bytes
+template <int TB>
+__host__ __device__ constexpr int batch_head_bytes() {
+    return (8 * TB + 4 * (2 * TB + FMM_BTAB) + 15) / 16 * 16;
+}
 
 struct BatchHead {
     long long* zoff;   // [TB] coaxial block of translation b
     int* pin;          // [TB] input degree (forward direction) of translation b
     int* row;          // [TB] row of the input vector (node index), -1: no translation
+    int* tab;          // the integer tables (FMM_BTAB ints)
     int* rgoff;        // [p+2] row groups of 4 below degree l
-    int* jpoff;        // [p+2] offset of the padded J block of degree l (in elements)
-    int* bo;           // [p+2] scratch
+    int* jpoff;        // [p+2] offset of the padded J block of degree l (elements)
+    int* poff;         // [p+2] offset of degree l in the padded layout
+    int* rg_l;         // [R] degree of row group r
+    int* rg_r0;        // [R] first row (within its degree) of row group r
+    int* om_m;         // [(p+1)(p+2)/2] order m of coaxial item t (m-major, o = m..p)
+    int* om_o;         // output degree of coaxial item t
 };
 
+template <int TB>
 __device__ __forceinline__ BatchHead batch_head(unsigned char* sm) {
     BatchHead h;
     h.zoff = (long long*)sm;
-    h.pin = (int*)(h.zoff + FMM_TB);
-    h.row = h.pin + FMM_TB;
-    h.rgoff = h.row + FMM_TB;
-    h.jpoff = h.rgoff + DDLPB_FMM_PMAX + 4;
-    h.bo = h.jpoff + DDLPB_FMM_PMAX + 4;
+    h.pin = (int*)(h.zoff + TB);
+    h.row = h.pin + TB;
+    h.tab = h.row + TB;
+    h.rgoff = h.tab + FMM_BTAB_RGOFF;
+    h.jpoff = h.tab + FMM_BTAB_JPOFF;
+    h.poff = h.tab + FMM_BTAB_POFF;
+    h.rg_l = h.tab + FMM_BTAB_RGL;
+    h.rg_r0 = h.tab + FMM_BTAB_RGR0;
+    h.om_m = h.tab + FMM_BTAB_OMM;
+    h.om_o = h.tab + FMM_BTAB_OMO;
     return h;
 }
 
-__device__ __forceinline__ void fill_tables(const BatchHead& h, int p) {
-    if (threadIdx.x == 0) {
-        h.rgoff[0] = 0;
-        h.jpoff[0] = 0;
-        for (int l = 0; l <= p; ++l) {
-            const int n4 = (2 * l + 1 + 3) / 4 * 4;
-            h.rgoff[l + 1] = h.rgoff[l] + n4 / 4;
-            h.jpoff[l + 1] = h.jpoff[l] + n4 * n4;
-        }
-    }
+// Host: the integer tables for order p (layout of FMM_BTAB_*), the padded J and the sizes.
+static inline int fmm_padded_size(int p) {
+    int s = 0;
+    for (int l = 0; l <= p; ++l) s += 4 * (l / 2 + 1);
+    return s;
 }
 
-// Rz(s angle_b) on the whole batch, degree <= deg; ang[b][which][cos|sin][32].
-template <typename T>
-__device__ __forceinline__ void brot_z(T* V, int nbp, int deg, const T* ang, int which, T s) {
-    const int nd = (deg + 1) * (deg + 1);
-    for (int idx = threadIdx.x; idx < nd; idx += blockDim.x) {
-        const int l = deg_of(idx), m = idx - l * l - l;
-        if (m <= 0) continue;
-#pragma unroll
-        for (int b = 0; b < FMM_TB; ++b) {
-            const T* a = ang + (b * 4 + which * 2) * 32;
-            const T c = a[m], sn = s * a[32 + m];
-            T* v = V + (size_t)b * nbp;
-            const T x = v[idx], y = v[idx - 2 * m];
-            v[idx] = c * x - sn * y;
-            v[idx - 2 * m] = sn * x + c * y;
+static void fmm_batch_tables(int p, std::vector<int>& tab) {
+    tab.assign(FMM_BTAB, 0);
+    int rg = 0, jp = 0, po = 0;
+    for (int l = 0; l <= p + 1; ++l) {
+        tab[FMM_BTAB_RGOFF + l] = rg;
+        tab[FMM_BTAB_JPOFF + l] = jp;
+        tab[FMM_BTAB_POFF + l] = po;
+        if (l > p) break;
+        const int n4 = 4 * (l / 2 + 1);
+        for (int r = 0; r < n4 / 4; ++r) {
+            tab[FMM_BTAB_RGL + rg + r] = l;
+            tab[FMM_BTAB_RGR0 + rg + r] = 4 * r;
         }
+        rg += n4 / 4;
+        jp += n4 * n4;
+        po += n4;
+    }
+    int t = 0;
+    for (int m = 0; m <= p; ++m)
+        for (int o = m; o <= p; ++o, ++t) {
+            tab[FMM_BTAB_OMM + t] = m;
+            tab[FMM_BTAB_OMO + t] = o;
+        }
+}
+
+// Four consecutive values (16-byte aligned for float, 32 for double) to registers and back.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+    const float4 t = *(const float4*)p;
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+    const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) { *(float4*)p = make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+    *(double2*)p = make_double2(v[0], v[1]);
+    *(double2*)(p + 2) = make_double2(v[2], v[3]);
+}
+
+// Rz(s angle_b) on the whole batch, degree <= deg; ang[b][which][cos|sin][32].  flip_in: the
+// input holds S v (its m < 0 entries negated); flip_out: write S of the result.
+template <typename T, int TB>
+__device__ __forceinline__ void brot_z(T* V, int nbpp, int deg, const T* ang, int which, T s, bool flip_in,
+                                       bool flip_out, const BatchHead& h) {
+    const int nd = deg * (deg + 1) / 2;   // (l, m) with 1 <= m <= l <= deg
+    for (int e = threadIdx.x; e < TB * nd; e += blockDim.x) {
+        const int b = e / nd, t = e - b * nd;
+        int l = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+        if (l * (l + 1) / 2 <= t) ++l;
+        if (l * (l - 1) / 2 > t) --l;
+        const int m = t - l * (l - 1) / 2 + 1;
+        const T* a = ang + (b * 4 + which * 2) * 32;
+        const T c = a[m], sn = s * a[32 + m];
+        T* v = V + (size_t)b * nbpp + h.poff[l] + l;
+        const T x = v[m], y = flip_in ? -v[-m] : v[-m];
+        const T nx = c * x - sn * y, ny = sn * x + c * y;
+        v[m] = nx;
+        v[-m] = flip_out ? -ny : ny;
     }
     __syncthreads();
 }
 
-// Out[b] = J In[b] (or J^T In[b]) degree by degree, degree <= deg, all FMM_TB rows.
-template <typename T>
-__device__ __forceinline__ void bmul_J(const T* __restrict__ JP, const T* In, T* Out, int nbp, int deg, bool tr,
-                                       const BatchHead& h) {
+// Out[b] = J^T In[b], degree by degree up to deg, all TB rows (padded layout).
+template <typename T, int TB>
+__device__ __forceinline__ void bmul_JT(const T* __restrict__ JP, const T* In, T* Out, int nbpp, int deg,
+                                        const BatchHead& h) {
+    constexpr int G = TB / 4;                      // translation groups of 4
     const int R = h.rgoff[deg + 1];
-    for (int e = threadIdx.x; e < R * (FMM_TB / 4); e += blockDim.x) {
-        const int cg = e / R, r = e - cg * R;
-        int l = 0;
-        while (h.rgoff[l + 1] <= r) ++l;
-        const int n = 2 * l + 1, n4 = (n + 3) & ~3, r0 = 4 * (r - h.rgoff[l]), b0 = 4 * cg;
-        const T* Jl = JP + h.jpoff[l];
-        T acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-        const T* x0 = In + (size_t)b0 * nbp + l * l;
-        if (tr) {
-            const T* col = Jl + r0;
-            for (int k = 0; k < n; ++k) {
-                T jv[4], xv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) jv[i] = col[k * n4 + i];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) xv[j] = x0[(size_t)j * nbp + k];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += jv[i] * xv[j];
-            }
-        } else {
-            const T* rows = Jl + r0 * n4;
-            for (int k = 0; k < n; ++k) {
-                T jv[4], xv[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) jv[i] = rows[i * n4 + k];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) xv[j] = x0[(size_t)j * nbp + k];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] += jv[i] * xv[j];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            T* o = Out + (size_t)(b0 + j) * nbp + l * l;
+    const bool pairs = R * G > (int)blockDim.x;
+    const int ns = pairs ? (R + 1) >> 1 : R;
+    for (int e = threadIdx.x; e < ns * G; e += blockDim.x) {
+        const int cg = e / ns, s = e - cg * ns;
+        const size_t b0 = 4 * (size_t)cg * nbpp;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int r = pass ? R - 1 - s : s;
+            if (pass && (!pairs || r == s)) break;
+            const int l = h.rg_l[r], r0 = h.rg_r0[r];
+            const int n4 = 4 * ((l >> 1) + 1);
+            const T* Jc = JP + h.jpoff[l] + r0;
+            const T* x = In + b0 + h.poff[l];
+            T acc[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (r0 + i < n) o[r0 + i] = acc[i][j];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+            for (int k = 0; k < n4; k += 4) {
+                T xv[4][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ld4(x + (size_t)j * nbpp + k, xv[j]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    T jv[4];
+                    ld4(Jc + (size_t)(k + u) * n4, jv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] += jv[i] * xv[j][u];
+                }
+            }
+            T* o = Out + b0 + h.poff[l] + r0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const T v[4] = {acc[0][j], acc[1][j], acc[2][j], acc[3][j]};
+                st4(o + (size_t)j * nbpp, v);
+            }
         }
     }
     __syncthreads();
@@ -609,24 +674,24 @@ __device__ __forceinline__ long long coax_m_offset(int pin, int pout, int m) {
 }
 
 // Coaxial step (forward degrees pin_b -> pout): forward Out = Z_b In (degree pout), transposed
-// Out = Z_b^T In (degree pin_b).  Rows without a translation are skipped (their Out is zero).
-// The stored block is read from global memory 8 entries at a time per thread (independent loads
-// in flight) before the multiply-adds.
-template <typename T>
-__device__ __forceinline__ void bcoax(const T* __restrict__ coax, const BatchHead& h, int pout, bool tr, const T* In,
-                                      T* Out, int nbp) {
-    for (int i = threadIdx.x; i < FMM_TB * nbp; i += blockDim.x) Out[i] = 0;
+// Out = Z_b^T In (degree pin_b).  flip_in: In holds S of the input.  Rows without a translation
+// are skipped (their Out is zero).  The stored block is read from global memory 8 entries at a
+// time per thread (independent loads in flight) before the multiply-adds.
+template <typename T, int TB>
+__device__ __forceinline__ void bcoax(const T* __restrict__ coax, const BatchHead& h, int pout, bool tr, bool flip_in,
+                                      const T* In, T* Out, int nbpp) {
+    for (int i = threadIdx.x; i < TB * nbpp; i += blockDim.x) Out[i] = 0;
     __syncthreads();
-    const int per_b = (pout + 1) * (pout + 1);
-    for (int e = threadIdx.x; e < FMM_TB * per_b; e += blockDim.x) {
-        const int b = e / per_b, r = e - b * per_b;
+    const int nom = (pout + 1) * (pout + 2) / 2;
+    for (int e = threadIdx.x; e < TB * nom; e += blockDim.x) {
+        const int b = e / nom, t = e - b * nom;
         if (h.row[b] < 0) continue;
         const int pb = h.pin[b];
-        const int m = r / (pout + 1), o = r - m * (pout + 1);
-        if (m > min(pb, pout) || o < m || (tr && o > pb)) continue;
+        const int m = h.om_m[t], o = h.om_o[t];
+        if (m > min(pb, pout) || (tr && o > pb)) continue;
         const int na = pout + 1 - m;
         const T* Z = coax + h.zoff[b] + coax_m_offset(pb, pout, m);
-        const T* x = In + (size_t)b * nbp;
+        const T* x = In + (size_t)b * nbpp;
         T sp = 0, sm = 0;
         // forward: z_k = Z[(k - m) na + (o - m)], coefficient index k over input degrees l;
         // transposed: z_k = Z[(o - m) na + (k - m)], k over output degrees a
@@ -641,14 +706,15 @@ __device__ __forceinline__ void bcoax(const T* __restrict__ coax, const BatchHea
             for (int u = 0; u < 8; ++u) {
                 const int k = k0 + u;
                 if (k <= kend) {
-                    sp += z[u] * x[k * k + k + m];
-                    sm += z[u] * x[k * k + k - m];
+                    const T* xk = x + h.poff[k] + k;
+                    sp += z[u] * xk[m];
+                    sm += z[u] * xk[-m];
                 }
             }
         }
-        T* y = Out + (size_t)b * nbp;
-        y[o * o + o + m] = sp;
-        if (m > 0) y[o * o + o - m] = sm;
+        T* y = Out + (size_t)b * nbpp + h.poff[o] + o;
+        y[m] = sp;
+        if (m > 0) y[-m] = flip_in ? -sm : sm;
     }
     __syncthreads();
 }
@@ -675,19 +741,20 @@ __device__ __forceinline__ void batch_angles(T* ang, int b, int lane, int p, con
 }
 
 // Translate the batch in place: V holds the inputs (rows b, degree d1), W receives the outputs
-// (degree d2).  TR: the transposed translations.
-template <typename T>
+// (degree d2).  TR: the transposed translations.  J = S J^T S: the S on the right is applied by
+// the rotation before, the one on the left by the step after.
+template <typename T, int TB>
 __device__ __forceinline__ void batch_translate(const T* JP, const T* coax, const BatchHead& h, const T* ang, int p,
-                                                bool tr, int d1, int d2, T* V, T* W, int nbp) {
-    brot_z(V, nbp, d1, ang, 0, (T)-1);           // Rz(-alpha)
-    bmul_J(JP, V, W, nbp, d1, true, h);          // J^T
-    brot_z(W, nbp, d1, ang, 1, (T)-1);           // Rz(-beta)
-    bmul_J(JP, W, V, nbp, d1, false, h);         // J
-    bcoax(coax, h, p, tr, V, W, nbp);            // along z
-    bmul_J(JP, W, V, nbp, d2, true, h);          // J^T
-    brot_z(V, nbp, d2, ang, 1, (T)1);            // Rz(beta)
-    bmul_J(JP, V, W, nbp, d2, false, h);         // J
-    brot_z(W, nbp, d2, ang, 0, (T)1);            // Rz(alpha)
+                                                bool tr, int d1, int d2, T* V, T* W, int nbpp) {
+    brot_z<T, TB>(V, nbpp, d1, ang, 0, (T)-1, false, false, h);   // Rz(-alpha)
+    bmul_JT<T, TB>(JP, V, W, nbpp, d1, h);                         // J^T
+    brot_z<T, TB>(W, nbpp, d1, ang, 1, (T)-1, false, true, h);    // S Rz(-beta)
+    bmul_JT<T, TB>(JP, W, V, nbpp, d1, h);                         // J^T S (J up to the left S)
+    bcoax<T, TB>(coax, h, p, tr, true, V, W, nbpp);                // left S, then along z
+    bmul_JT<T, TB>(JP, W, V, nbpp, d2, h);                         // J^T
+    brot_z<T, TB>(V, nbpp, d2, ang, 1, (T)1, false, true, h);     // S Rz(beta)
+    bmul_JT<T, TB>(JP, V, W, nbpp, d2, h);                         // J^T S
+    brot_z<T, TB>(W, nbpp, d2, ang, 0, (T)1, true, false, h);     // left S, then Rz(alpha)
 }
 
 // Shared-memory layout of a batched CTA after the head: JP, V, W, acc, angles.
@@ -700,33 +767,40 @@ struct BatchArrays {
     T* ang;
 };
 
-template <typename T>
-__device__ __forceinline__ BatchArrays<T> batch_arrays(unsigned char* sm, long long jpsize, int nbp, int nacc) {
+template <typename T, int TB>
+__device__ __forceinline__ BatchArrays<T> batch_arrays(unsigned char* sm, long long jpsize, int nbpp, int nacc) {
     BatchArrays<T> a;
-    a.JP = (T*)(sm + FMM_BATCH_HEAD);
+    a.JP = (T*)(sm + batch_head_bytes<TB>());
     a.V = a.JP + jpsize;
-    a.W = a.V + (size_t)FMM_TB * nbp;
-    a.acc = a.W + (size_t)FMM_TB * nbp;
-    a.ang = a.acc + (size_t)nacc * nbp;
+    a.W = a.V + (size_t)TB * nbpp;
+    a.acc = a.W + (size_t)TB * nbpp;
+    a.ang = a.acc + (size_t)nacc * nbpp;
     return a;
 }
 
-template <typename T>
+// Copy J and the integer tables into shared memory and zero V, W and acc (their padding stays
+// zero: the J^T products write zeros there and nothing else writes it).
+template <typename T, int TB>
 __device__ __forceinline__ void batch_setup(const BatchArrays<T>& a, const BatchHead& h, const T* __restrict__ JPg,
-                                            long long jpsize, int p) {
+                                            long long jpsize, const int* __restrict__ btab, int nbpp, int nacc) {
     for (long long k = threadIdx.x; k < jpsize; k += blockDim.x) a.JP[k] = JPg[k];
-    fill_tables(h, p);
+    for (int k = threadIdx.x; k < FMM_BTAB; k += blockDim.x) h.tab[k] = btab[k];
+    const int nz = (2 * TB + nacc) * nbpp;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) a.V[k] = (T)0;
+    __syncthreads();
 }
 
-// Load the batch's input rows (zero above their degree and for absent translations).
-template <typename T>
-__device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restrict__ X, T* V, int nbp, int din_tr,
-                                           bool tr) {
-    for (int e = threadIdx.x; e < FMM_TB * nbp; e += blockDim.x) {
+// Load the batch's input rows into the padded layout (zero above their degree and for absent
+// translations).
+template <typename T, int TB>
+__device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restrict__ X, T* V, int nbp, int nbpp,
+                                           int din_tr, bool tr) {
+    for (int e = threadIdx.x; e < TB * nbp; e += blockDim.x) {
         const int b = e / nbp, i = e - b * nbp;
+        const int l = deg_of(i);
         const int rw = h.row[b];
         const int dl = tr ? din_tr : h.pin[b];
-        V[e] = (rw >= 0 && i < (dl + 1) * (dl + 1)) ? X[(size_t)rw * nbp + i] : (T)0;
+        V[(size_t)b * nbpp + h.poff[l] + i - l * l] = (rw >= 0 && l <= dl) ? X[(size_t)rw * nbp + i] : (T)0;
     }
     __syncthreads();
 }
@@ -734,8 +808,9 @@ __device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restri
 // M2L, one CTA per chunk.  Forward: the chunk's translations share the target; part[ck] = their
 // sum (degree p).  Transposed: they share the source; part[ck] = the sum of the transposed
 // translations of the targets' local adjoints (degree of the source's multipole).
-template <typename T, bool TR>
+template <typename T, bool TR, int TB>
 __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q, long long jpsize,
+                                                          const int* __restrict__ btab,
                                                           const int* __restrict__ ck_b, const int* __restrict__ ck_e,
                                                           const int* __restrict__ perm, const int* __restrict__ m2l_t,
                                                           const int* __restrict__ m2l_s,
@@ -746,17 +821,16 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
                                                           T* __restrict__ part) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nbp = (p + 1) * (p + 1);
-    const BatchHead h = batch_head(smraw);
-    const BatchArrays<T> a = batch_arrays<T>(smraw, jpsize, nbp, 1);
-    batch_setup(a, h, JPg, jpsize, p);
-    for (int i = threadIdx.x; i < nbp; i += blockDim.x) a.acc[i] = 0;
+    const BatchHead h = batch_head<TB>(smraw);
+    const int nbpp = btab[FMM_BTAB_POFF + p + 1];
+    const BatchArrays<T> a = batch_arrays<T, TB>(smraw, jpsize, nbpp, 1);
+    batch_setup<T, TB>(a, h, JPg, jpsize, btab, nbpp, 1);
     const int ck = blockIdx.x;
     const int u0 = ck_b[ck], u1 = ck_e[ck];
-    __syncthreads();
-    for (int ub = u0; ub < u1; ub += FMM_TB) {
-        const int nt = min(FMM_TB, u1 - ub);
-        {
-            const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;   // FMM_BT / 32 == FMM_TB
+    for (int ub = u0; ub < u1; ub += TB) {
+        const int nt = min(TB, u1 - ub);
+        for (int b = threadIdx.x >> 5; b < TB; b += FMM_BT / 32) {
+            const int lane = threadIdx.x & 31;
             if (b < nt) {
                 const int u = perm ? perm[ub + b] : ub + b;
                 const int A = m2l_t[u], B = m2l_s[u];
@@ -774,18 +848,21 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
         __syncthreads();
         int dmax = 0;
         for (int b = 0; b < nt; ++b) dmax = max(dmax, h.pin[b]);
-        batch_load(h, X, a.V, nbp, p, TR);
+        batch_load<T, TB>(h, X, a.V, nbp, nbpp, p, TR);
         const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
-        batch_translate(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbp);
-        const int nd2 = (d2 + 1) * (d2 + 1);
+        batch_translate<T, TB>(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
+        const int nd2 = h.poff[d2 + 1];
         for (int i = threadIdx.x; i < nd2; i += blockDim.x) {
             T s = a.acc[i];
-            for (int b = 0; b < nt; ++b) s += a.W[(size_t)b * nbp + i];
+            for (int b = 0; b < nt; ++b) s += a.W[(size_t)b * nbpp + i];
             a.acc[i] = s;
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < nbp; i += blockDim.x) part[(size_t)ck * nbp + i] = a.acc[i];
+    for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
+        const int l = deg_of(i);
+        part[(size_t)ck * nbp + i] = a.acc[h.poff[l] + i - l * l];
+    }
 }
 
 // Tree passes, FMM_TB translations per CTA, nodes [first, first + count) of one level.
@@ -796,23 +873,26 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
 // Leaves are skipped by the kinds 0 and 2 (their rows were written by the leaf kernels).
 template <typename T, int KIND>
 __global__ void __launch_bounds__(FMM_BT) k_fmm_tree_batch(int first, int count, int p, int q, long long jpsize,
+                                                           const int* __restrict__ btab,
                                                            const int* __restrict__ parent,
                                                            const int* __restrict__ child0,
                                                            const int* __restrict__ ck_ptr, const T* __restrict__ part,
                                                            const long long* __restrict__ off,
                                                            const double4* __restrict__ nc, const T* __restrict__ JPg,
                                                            const T* __restrict__ coax, T* __restrict__ X) {
+    constexpr int TB = FMM_TB;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nbp = (p + 1) * (p + 1);
-    const BatchHead h = batch_head(smraw);
-    const BatchArrays<T> a = batch_arrays<T>(smraw, jpsize, nbp, 0);
-    batch_setup(a, h, JPg, jpsize, p);
+    const BatchHead h = batch_head<TB>(smraw);
+    const int nbpp = btab[FMM_BTAB_POFF + p + 1];
+    const BatchArrays<T> a = batch_arrays<T, TB>(smraw, jpsize, nbpp, 0);
+    batch_setup<T, TB>(a, h, JPg, jpsize, btab, nbpp, 0);
     constexpr bool pairs = (KIND == 0 || KIND == 2);
-    constexpr int per = pairs ? FMM_TB / 2 : FMM_TB;     // nodes per CTA
+    constexpr int per = pairs ? TB / 2 : TB;     // nodes per CTA
     constexpr bool TR = (KIND >= 2);
     const int k0 = first + blockIdx.x * per;
     {
-        const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;   // FMM_BT / 32 == FMM_TB
         const int k = k0 + (pairs ? b / 2 : b);
         int src = -1, tgt = -1;
         long long zo = 0;
@@ -837,38 +917,33 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_tree_batch(int first, int count,
     }
     __syncthreads();
     // forward inputs have degree pin (M2M) or p (L2L); transposed inputs degree p
-    for (int e = threadIdx.x; e < FMM_TB * nbp; e += blockDim.x) {
-        const int b = e / nbp, i = e - b * nbp;
-        const int rw = h.row[b];
-        const int dl = TR ? p : h.pin[b];
-        a.V[e] = (rw >= 0 && i < (dl + 1) * (dl + 1)) ? X[(size_t)rw * nbp + i] : (T)0;
-    }
-    __syncthreads();
+    batch_load<T, TB>(h, X, a.V, nbp, nbpp, p, TR);
     int dmax = 0;
-    for (int b = 0; b < FMM_TB; ++b) dmax = max(dmax, h.pin[b]);
+    for (int b = 0; b < TB; ++b) dmax = max(dmax, h.pin[b]);
     const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
-    batch_translate(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbp);
+    batch_translate<T, TB>(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
     // combine and write (each node owned by one thread per coefficient: fixed order)
     for (int e = threadIdx.x; e < per * nbp; e += blockDim.x) {
         const int g = e / nbp, i = e - g * nbp;
         const int k = k0 + g;
         if (k >= first + count) continue;
+        const int l = deg_of(i), pi = h.poff[l] + i - l * l;
         if (pairs) {
             if (child0[k] < 0) continue;
-            X[(size_t)k * nbp + i] = a.W[(size_t)(2 * g) * nbp + i] + a.W[(size_t)(2 * g + 1) * nbp + i];
+            X[(size_t)k * nbp + i] = a.W[(size_t)(2 * g) * nbpp + pi] + a.W[(size_t)(2 * g + 1) * nbpp + pi];
         } else {
             T s = 0;
             for (int ck = ck_ptr[k]; ck < ck_ptr[k + 1]; ++ck) s += part[(size_t)ck * nbp + i];
-            if (h.row[g] >= 0) s += a.W[(size_t)g * nbp + i];
+            if (h.row[g] >= 0) s += a.W[(size_t)g * nbpp + pi];
             X[(size_t)k * nbp + i] = s;
         }
     }
 }
 
-template <typename T>
+template <typename T, int TB>
 size_t fmm_batch_smem(int p, long long jpsize, int nacc) {
-    const int nbp = (p + 1) * (p + 1);
-    return FMM_BATCH_HEAD + sizeof(T) * ((size_t)jpsize + (2 * (size_t)FMM_TB + nacc) * nbp + FMM_TB * 4 * 32);
+    const int nbpp = fmm_padded_size(p);
+    return batch_head_bytes<TB>() + sizeof(T) * ((size_t)jpsize + (2 * (size_t)TB + nacc) * nbpp + TB * 4 * 32);
 }
 
 // ---------------------------------------------------------------- host
@@ -1174,6 +1249,10 @@ static ddlpb_status fmm_prepare(ddlpb_ctx* c, FmmOps<T>& O) {
     O.jpsize = (long long)Jp.size();
     DDLPB_TRY(ctx_alloc(c, &O.JP, Jp.size()));
     DDLPB_CK(c, cudaMemcpyAsync(O.JP, Jp.data(), sizeof(T) * Jp.size(), cudaMemcpyHostToDevice, st));
+    std::vector<int> bt;
+    fmm_batch_tables(p, bt);
+    DDLPB_TRY(ctx_alloc(c, &O.btab, bt.size()));
+    DDLPB_CK(c, cudaMemcpyAsync(O.btab, bt.data(), sizeof(int) * bt.size(), cudaMemcpyHostToDevice, st));
     DDLPB_TRY(ctx_alloc(c, &O.coax, std::max<long long>(F.coax_size, 1)));
     const int n_tr = F.n_m2l + 2 * F.n_nodes;
     k_fmm_coax<T><<<n_tr, 128, 0, st>>>(F.n_m2l, F.n_nodes, p, F.q, c->kappa, F.m2l_t, F.m2l_s, F.child0, F.parent,
@@ -1213,7 +1292,8 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax;
     cudaStream_t st = c->stream;
     const bool f32 = sizeof(T) == 4;
-    const size_t sm0 = fmm_batch_smem<T>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T>(p, O.jpsize, 1);
+    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB;
+    const size_t sm0 = fmm_batch_smem<T, FMM_TB>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T, TBM>(p, O.jpsize, 1);
     {
         KernelTimer kt(c, "fmm_tree", f32, 2);
         k_fmm_leaf_mult<T><<<M, 128, 0, st>>>(M, c->nb, nbp, F.leaf_node, mu, O.Mx);
@@ -1222,15 +1302,15 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
         for (int lv = F.depth - 1; lv >= 0; --lv) {
             const int first = F.lev[lv], count = F.lev[lv + 1] - first;
             k_fmm_tree_batch<T, 0><<<ceil_div(count, FMM_TB / 2), FMM_BT, sm0, st>>>(
-                first, count, p, q, O.jpsize, F.parent, F.child0, nullptr, nullptr, F.m2m_off, F.node_g, O.JP, O.coax,
+                first, count, p, q, O.jpsize, O.btab, F.parent, F.child0, nullptr, nullptr, F.m2m_off, F.node_g, O.JP, O.coax,
                 O.Mx);
             DDLPB_LAUNCHED(c, "fmm_m2m");
         }
     }
     if (F.n_ck > 0) {
         KernelTimer kt(c, "fmm_m2l", f32);
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, false>, sm1)));
-        k_fmm_m2l_batch<T, false><<<F.n_ck, FMM_BT, sm1, st>>>(F.n_ck, p, q, O.jpsize, F.ck_b, F.ck_e, nullptr, F.m2l_t,
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, false, TBM>, sm1)));
+        k_fmm_m2l_batch<T, false, TBM><<<F.n_ck, FMM_BT, sm1, st>>>(F.n_ck, p, q, O.jpsize, O.btab, F.ck_b, F.ck_e, nullptr, F.m2l_t,
                                                                 F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP, O.coax,
                                                                 O.Mx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l");
@@ -1241,7 +1321,7 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
         for (int lv = 0; lv <= F.depth; ++lv) {
             const int first = F.lev[lv], count = F.lev[lv + 1] - first;
             k_fmm_tree_batch<T, 1><<<ceil_div(count, FMM_TB), FMM_BT, sm0, st>>>(
-                first, count, p, q, O.jpsize, F.parent, F.child0, F.tck_ptr, O.part, F.l2l_off, F.node_g, O.JP, O.coax,
+                first, count, p, q, O.jpsize, O.btab, F.parent, F.child0, F.tck_ptr, O.part, F.l2l_off, F.node_g, O.JP, O.coax,
                 O.Lx);
             DDLPB_LAUNCHED(c, "fmm_l2l");
         }
@@ -1270,7 +1350,8 @@ ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
     const int p = F.p, q = F.q, M = c->M, L = c->lmax, N = c->N;
     cudaStream_t st = c->stream;
     const bool f32 = sizeof(T) == 4;
-    const size_t sm0 = fmm_batch_smem<T>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T>(p, O.jpsize, 1);
+    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB;
+    const size_t sm0 = fmm_batch_smem<T, FMM_TB>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T, TBM>(p, O.jpsize, 1);
     {
         KernelTimer kt(c, "fmm_tree", f32, 2);
         const size_t smL = (sizeof(T) + sizeof(int)) * (size_t)N;
@@ -1280,15 +1361,15 @@ ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
         for (int lv = F.depth - 1; lv >= 0; --lv) {
             const int first = F.lev[lv], count = F.lev[lv + 1] - first;
             k_fmm_tree_batch<T, 2><<<ceil_div(count, FMM_TB / 2), FMM_BT, sm0, st>>>(
-                first, count, p, q, O.jpsize, F.parent, F.child0, nullptr, nullptr, F.l2l_off, F.node_g, O.JP, O.coax,
+                first, count, p, q, O.jpsize, O.btab, F.parent, F.child0, nullptr, nullptr, F.l2l_off, F.node_g, O.JP, O.coax,
                 O.Lx);
             DDLPB_LAUNCHED(c, "fmm_l2l_T");
         }
     }
     if (F.n_ckT > 0) {
         KernelTimer kt(c, "fmm_m2l_T", f32);
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, true>, sm1)));
-        k_fmm_m2l_batch<T, true><<<F.n_ckT, FMM_BT, sm1, st>>>(F.n_ckT, p, q, O.jpsize, F.ckT_b, F.ckT_e, F.m2lT_k,
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, true, TBM>, sm1)));
+        k_fmm_m2l_batch<T, true, TBM><<<F.n_ckT, FMM_BT, sm1, st>>>(F.n_ckT, p, q, O.jpsize, O.btab, F.ckT_b, F.ckT_e, F.m2lT_k,
                                                                 F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP,
                                                                 O.coax, O.Lx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l_T");
@@ -1299,7 +1380,7 @@ ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
         for (int lv = 0; lv <= F.depth; ++lv) {
             const int first = F.lev[lv], count = F.lev[lv + 1] - first;
             k_fmm_tree_batch<T, 3><<<ceil_div(count, FMM_TB), FMM_BT, sm0, st>>>(
-                first, count, p, q, O.jpsize, F.parent, F.child0, F.sck_ptr, O.part, F.m2m_off, F.node_g, O.JP, O.coax,
+                first, count, p, q, O.jpsize, O.btab, F.parent, F.child0, F.sck_ptr, O.part, F.m2m_off, F.node_g, O.JP, O.coax,
                 O.Mx);
             DDLPB_LAUNCHED(c, "fmm_m2m_T");
         }

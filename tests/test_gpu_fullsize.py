@@ -19,7 +19,8 @@ Properties: the A block reproduces solid harmonics of degree <= lmax and the B b
 exp(kappa u.x) (the identities the oracle is pinned to) in every precision of the operators; the
 central difference of the energy along a random displacement field equals -sum F.v (FP64,
 direct coupling, where the forces are the exact gradient of the discrete energy); zero net
-force; the bench configuration's energy and forces against the FP64 direct result.
+force (exact for the direct coupling, to the FMM error in FMM mode); the bench configuration's
+energy and forces against the FP64 direct result.
 """
 import numpy as np
 import pytest
@@ -163,10 +164,10 @@ def test_1000_sas_bench_configuration_rows(w1000):
 
 def test_1000_sas_energy_forces(w1000):
     """The bench configuration's energy and forces against the FP64 direct solution (FMM
-    truncation plus the 1e-8 solver tolerance), zero net force in both, and the directional
-    derivative of the FP64 direct energy along a random displacement field by central
-    differences (h = 3e-4 bohr: the O(h^2) truncation is about 2e-6 of |F| |v| there, the solver
-    noise 1e-11 |E| / h below 1e-7)."""
+    truncation plus the 1e-8 solver tolerance), zero net force (exact for the direct coupling,
+    to the FMM error with the FMM), and the directional derivative of the FP64 direct energy
+    along a random displacement field by central differences (h = 3e-4 bohr: the O(h^2)
+    truncation is about 2e-6 of |F| |v| there, the solver noise 1e-11 |E| / h below 1e-7)."""
     w = w1000["w"]
     ctx = context(w)
     ctx.solve()
@@ -178,8 +179,10 @@ def test_1000_sas_energy_forces(w1000):
     ref.adjoint()
     E64, F64 = ref.energy(), ref.forces()
     ref.close()
-    for f in (F, F64):
-        assert np.abs(f.sum(0)).max() <= 1e-8 * np.abs(f).max()
+    # zero net force: exact for the direct coupling (to rounding); in FMM mode the far field is
+    # approximated and the net force is of the order of the FMM error (4e-7 relative measured)
+    assert np.abs(F64.sum(0)).max() <= 1e-12 * np.abs(F64).max()
+    assert np.abs(F.sum(0)).max() <= 2e-6 * np.abs(F).max()
     assert abs(E - E64) <= 1e-6 * abs(E64), (E, E64)
     assert np.linalg.norm(F - F64) <= 1e-5 * np.linalg.norm(F64)
 
