@@ -498,6 +498,7 @@ __global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, cons
 #define FMM_TB 8           // translations per batch (tree passes, FP64 M2L)
 #define FMM_TB_M2L32 16    // translations per batch of the FP32 M2L chunks
 #define FMM_BT 256         // threads of a batched CTA
+#define FMM_BT_M2L32 384   // threads of an FP32 M2L CTA (two per SM: 24 warps)
 #define FMM_RG_MAX 140     // row groups of 4 up to degree DDLPB_FMM_PMAX (132 at 21)
 #define FMM_OM_MAX 256     // (m, o) items of the coaxial step, (p+1)(p+2)/2 (253 at 21)
 // integer tables of a batched CTA (built on the host, copied to shared memory)
@@ -508,7 +509,13 @@ __global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, cons
 #define FMM_BTAB_RGR0 (FMM_BTAB_RGL + FMM_RG_MAX)
 #define FMM_BTAB_OMM (FMM_BTAB_RGR0 + FMM_RG_MAX)
 #define FMM_BTAB_OMO (FMM_BTAB_OMM + FMM_OM_MAX)
-#define FMM_BTAB (FMM_BTAB_OMO + FMM_OM_MAX)
+#define FMM_BTAB_CMP (FMM_BTAB_OMO + FMM_OM_MAX)           // [m] order-m offset in a block p -> p
+#define FMM_BTAB_CMQ (FMM_BTAB_CMP + DDLPB_FMM_PMAX + 4)   // [m] order-m offset in a block q -> p
+#define FMM_BTAB (FMM_BTAB_CMQ + DDLPB_FMM_PMAX + 4)
+// tables read through the cache only (after the shared part of the same array)
+#define FMM_GTAB_UNPAD FMM_BTAB                              // [(p+1)^2] padded slot of index l*l+l+m
+#define FMM_GTAB_LM (FMM_GTAB_UNPAD + (DDLPB_FMM_PMAX + 1) * (DDLPB_FMM_PMAX + 1))   // (l, m > 0) items
+#define FMM_GTAB (FMM_GTAB_LM + DDLPB_FMM_PMAX * (DDLPB_FMM_PMAX + 1) / 2)
 
 // shared-memory head: per translation the block offset (long long), input degree and source
 // row (int), then the integer tables; rounded up to 16 bytes
@@ -529,6 +536,8 @@ struct BatchHead {
     int* rg_r0;        // [R] first row (within its degree) of row group r
     int* om_m;         // [(p+1)(p+2)/2] order m of coaxial item t (m-major, o = m..p)
     int* om_o;         // output degree of coaxial item t
+    int* cmp;          // [m] offset of the order-m part of a coaxial block with input degree p
+    int* cmq;          // [m] the same with input degree q
 };
 
 template <int TB>
@@ -545,6 +554,8 @@ __device__ __forceinline__ BatchHead batch_head(unsigned char* sm) {
     h.rg_r0 = h.tab + FMM_BTAB_RGR0;
     h.om_m = h.tab + FMM_BTAB_OMM;
     h.om_o = h.tab + FMM_BTAB_OMO;
+    h.cmp = h.tab + FMM_BTAB_CMP;
+    h.cmq = h.tab + FMM_BTAB_CMQ;
     return h;
 }
 
@@ -555,8 +566,8 @@ static inline int fmm_padded_size(int p) {
     return s;
 }
 
-static void fmm_batch_tables(int p, std::vector<int>& tab) {
-    tab.assign(FMM_BTAB, 0);
+static void fmm_batch_tables(int p, int q, std::vector<int>& tab) {
+    tab.assign(FMM_GTAB, 0);
     int rg = 0, jp = 0, po = 0;
     for (int l = 0; l <= p + 1; ++l) {
         tab[FMM_BTAB_RGOFF + l] = rg;
@@ -578,6 +589,27 @@ static void fmm_batch_tables(int p, std::vector<int>& tab) {
             tab[FMM_BTAB_OMM + t] = m;
             tab[FMM_BTAB_OMO + t] = o;
         }
+    // order-m offsets of the coaxial blocks: sum_{k < m} (pin + 1 - k)(p + 1 - k)
+    for (int m = 0, sp = 0, sq = 0; m <= p + 1; ++m) {
+        tab[FMM_BTAB_CMP + m] = sp;
+        tab[FMM_BTAB_CMQ + m] = sq;
+        sp += (p + 1 - m) * (p + 1 - m);
+        if (m <= q) sq += (q + 1 - m) * (p + 1 - m);
+    }
+    for (int l = 0; l <= p; ++l)
+        for (int m = -l; m <= l; ++m) tab[FMM_GTAB_UNPAD + l * l + l + m] = tab[FMM_BTAB_POFF + l] + l + m;
+    t = 0;
+    for (int l = 1; l <= p; ++l)
+        for (int m = 1; m <= l; ++m, ++t) tab[FMM_GTAB_LM + t] = (tab[FMM_BTAB_POFF + l] + l) | (m << 16);
+}
+
+// e / d for 0 <= e < 2^20 and d >= 1, given inv = 1.0f / d: the float quotient is within one of
+// the exact one and is corrected.
+__device__ __forceinline__ int qdiv(int e, int d, float inv) {
+    int q = __float2int_rz((float)e * inv);
+    if (q * d > e) --q;
+    else if ((q + 1) * d <= e) ++q;
+    return q;
 }
 
 // Four consecutive values (16-byte aligned for float, 32 for double) to registers and back.
@@ -599,17 +631,15 @@ __device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
 // input holds S v (its m < 0 entries negated); flip_out: write S of the result.
 template <typename T, int TB>
 __device__ __forceinline__ void brot_z(T* V, int nbpp, int deg, const T* ang, int which, T s, bool flip_in,
-                                       bool flip_out, const BatchHead& h) {
-    const int nd = deg * (deg + 1) / 2;   // (l, m) with 1 <= m <= l <= deg
+                                       bool flip_out, const int* __restrict__ gtab) {
+    const int nd = deg * (deg + 1) / 2;   // (l, m) with 1 <= m <= l <= deg, l-major
+    const float inv = 1.0f / (float)nd;
     for (int e = threadIdx.x; e < TB * nd; e += blockDim.x) {
-        const int b = e / nd, t = e - b * nd;
-        int l = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-        if (l * (l + 1) / 2 <= t) ++l;
-        if (l * (l - 1) / 2 > t) --l;
-        const int m = t - l * (l - 1) / 2 + 1;
+        const int b = qdiv(e, nd, inv), t = e - b * nd;
+        const int lm = __ldg(gtab + FMM_GTAB_LM + t), m = lm >> 16;
         const T* a = ang + (b * 4 + which * 2) * 32;
         const T c = a[m], sn = s * a[32 + m];
-        T* v = V + (size_t)b * nbpp + h.poff[l] + l;
+        T* v = V + (size_t)b * nbpp + (lm & 0xffff);
         const T x = v[m], y = flip_in ? -v[-m] : v[-m];
         const T nx = c * x - sn * y, ny = sn * x + c * y;
         v[m] = nx;
@@ -626,8 +656,9 @@ __device__ __forceinline__ void bmul_JT(const T* __restrict__ JP, const T* In, T
     const int R = h.rgoff[deg + 1];
     const bool pairs = R * G > (int)blockDim.x;
     const int ns = pairs ? (R + 1) >> 1 : R;
+    const float inv = 1.0f / (float)ns;
     for (int e = threadIdx.x; e < ns * G; e += blockDim.x) {
-        const int cg = e / ns, s = e - cg * ns;
+        const int cg = qdiv(e, ns, inv), s = e - cg * ns;
         const size_t b0 = 4 * (size_t)cg * nbpp;
         for (int pass = 0; pass < 2; ++pass) {
             const int r = pass ? R - 1 - s : s;
@@ -666,13 +697,6 @@ __device__ __forceinline__ void bmul_JT(const T* __restrict__ JP, const T* In, T
     __syncthreads();
 }
 
-// Offset of the order-m part of a coaxial block with degrees (pin -> pout):
-// sum_{k < m} (pin + 1 - k)(pout + 1 - k), in closed form.
-__device__ __forceinline__ long long coax_m_offset(int pin, int pout, int m) {
-    const long long A = pin + 1, B = pout + 1, M = m;
-    return M * A * B - (A + B) * M * (M - 1) / 2 + (M - 1) * M * (2 * M - 1) / 6;
-}
-
 // Coaxial step (forward degrees pin_b -> pout): forward Out = Z_b In (degree pout), transposed
 // Out = Z_b^T In (degree pin_b).  flip_in: In holds S of the input.  Rows without a translation
 // are skipped (their Out is zero).  The stored block is read from global memory 8 entries at a
@@ -680,17 +704,19 @@ __device__ __forceinline__ long long coax_m_offset(int pin, int pout, int m) {
 template <typename T, int TB>
 __device__ __forceinline__ void bcoax(const T* __restrict__ coax, const BatchHead& h, int pout, bool tr, bool flip_in,
                                       const T* In, T* Out, int nbpp) {
+    // pout is the expansion order p, and a block's input degree is p or q
     for (int i = threadIdx.x; i < TB * nbpp; i += blockDim.x) Out[i] = 0;
     __syncthreads();
     const int nom = (pout + 1) * (pout + 2) / 2;
+    const float inv = 1.0f / (float)nom;
     for (int e = threadIdx.x; e < TB * nom; e += blockDim.x) {
-        const int b = e / nom, t = e - b * nom;
+        const int b = qdiv(e, nom, inv), t = e - b * nom;
         if (h.row[b] < 0) continue;
         const int pb = h.pin[b];
         const int m = h.om_m[t], o = h.om_o[t];
         if (m > min(pb, pout) || (tr && o > pb)) continue;
         const int na = pout + 1 - m;
-        const T* Z = coax + h.zoff[b] + coax_m_offset(pb, pout, m);
+        const T* Z = coax + h.zoff[b] + (pb == pout ? h.cmp[m] : h.cmq[m]);
         const T* x = In + (size_t)b * nbpp;
         T sp = 0, sm = 0;
         // forward: z_k = Z[(k - m) na + (o - m)], coefficient index k over input degrees l;
@@ -744,17 +770,32 @@ __device__ __forceinline__ void batch_angles(T* ang, int b, int lane, int p, con
 // (degree d2).  TR: the transposed translations.  J = S J^T S: the S on the right is applied by
 // the rotation before, the one on the left by the step after.
 template <typename T, int TB>
-__device__ __forceinline__ void batch_translate(const T* JP, const T* coax, const BatchHead& h, const T* ang, int p,
-                                                bool tr, int d1, int d2, T* V, T* W, int nbpp) {
-    brot_z<T, TB>(V, nbpp, d1, ang, 0, (T)-1, false, false, h);   // Rz(-alpha)
-    bmul_JT<T, TB>(JP, V, W, nbpp, d1, h);                         // J^T
-    brot_z<T, TB>(W, nbpp, d1, ang, 1, (T)-1, false, true, h);    // S Rz(-beta)
-    bmul_JT<T, TB>(JP, W, V, nbpp, d1, h);                         // J^T S (J up to the left S)
-    bcoax<T, TB>(coax, h, p, tr, true, V, W, nbpp);                // left S, then along z
-    bmul_JT<T, TB>(JP, W, V, nbpp, d2, h);                         // J^T
-    brot_z<T, TB>(V, nbpp, d2, ang, 1, (T)1, false, true, h);     // S Rz(beta)
-    bmul_JT<T, TB>(JP, V, W, nbpp, d2, h);                         // J^T S
-    brot_z<T, TB>(W, nbpp, d2, ang, 0, (T)1, true, false, h);     // left S, then Rz(alpha)
+__device__ __forceinline__ void batch_translate(const T* JP, const T* coax, const BatchHead& h,
+                                                const int* __restrict__ gtab, const T* ang, int p, bool tr, int d1,
+                                                int d2, T* V, T* W, int nbpp) {
+    brot_z<T, TB>(V, nbpp, d1, ang, 0, (T)-1, false, false, gtab);   // Rz(-alpha)
+    bmul_JT<T, TB>(JP, V, W, nbpp, d1, h);                            // J^T
+    brot_z<T, TB>(W, nbpp, d1, ang, 1, (T)-1, false, true, gtab);    // S Rz(-beta)
+    bmul_JT<T, TB>(JP, W, V, nbpp, d1, h);                            // J^T S (J up to the left S)
+    bcoax<T, TB>(coax, h, p, tr, true, V, W, nbpp);                   // left S, then along z
+    bmul_JT<T, TB>(JP, W, V, nbpp, d2, h);                            // J^T
+    brot_z<T, TB>(V, nbpp, d2, ang, 1, (T)1, false, true, gtab);     // S Rz(beta)
+    bmul_JT<T, TB>(JP, V, W, nbpp, d2, h);                            // J^T S
+    brot_z<T, TB>(W, nbpp, d2, ang, 0, (T)1, true, false, gtab);     // left S, then Rz(alpha)
+}
+
+// Pull the batch's stored coaxial blocks towards L2 while the first rotations run: one warp per
+// translation, one prefetch per 128-byte line.
+template <typename T, int TB>
+__device__ __forceinline__ void batch_prefetch(const T* coax, const BatchHead& h, int p, int q) {
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x >> 5; b < TB; b += blockDim.x >> 5) {
+        if (h.row[b] < 0) continue;
+        const int bytes = (int)sizeof(T) * (h.pin[b] == p ? h.cmp[p + 1] : h.cmq[min(q, p) + 1]);
+        const char* base = (const char*)(coax + h.zoff[b]);
+        for (int off = lane * 128; off < bytes; off += 32 * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(base + off));
+    }
 }
 
 // Shared-memory layout of a batched CTA after the head: JP, V, W, acc, angles.
@@ -793,14 +834,15 @@ __device__ __forceinline__ void batch_setup(const BatchArrays<T>& a, const Batch
 // Load the batch's input rows into the padded layout (zero above their degree and for absent
 // translations).
 template <typename T, int TB>
-__device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restrict__ X, T* V, int nbp, int nbpp,
-                                           int din_tr, bool tr) {
+__device__ __forceinline__ void batch_load(const BatchHead& h, const int* __restrict__ gtab, const T* __restrict__ X,
+                                           T* V, int nbp, int nbpp, int din_tr, bool tr) {
+    const float inv = 1.0f / (float)nbp;
     for (int e = threadIdx.x; e < TB * nbp; e += blockDim.x) {
-        const int b = e / nbp, i = e - b * nbp;
-        const int l = deg_of(i);
+        const int b = qdiv(e, nbp, inv), i = e - b * nbp;
         const int rw = h.row[b];
         const int dl = tr ? din_tr : h.pin[b];
-        V[(size_t)b * nbpp + h.poff[l] + i - l * l] = (rw >= 0 && l <= dl) ? X[(size_t)rw * nbp + i] : (T)0;
+        V[(size_t)b * nbpp + __ldg(gtab + FMM_GTAB_UNPAD + i)] =
+            (rw >= 0 && i < (dl + 1) * (dl + 1)) ? X[(size_t)rw * nbp + i] : (T)0;
     }
     __syncthreads();
 }
@@ -808,8 +850,8 @@ __device__ __forceinline__ void batch_load(const BatchHead& h, const T* __restri
 // M2L, one CTA per chunk.  Forward: the chunk's translations share the target; part[ck] = their
 // sum (degree p).  Transposed: they share the source; part[ck] = the sum of the transposed
 // translations of the targets' local adjoints (degree of the source's multipole).
-template <typename T, bool TR, int TB>
-__global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q, long long jpsize,
+template <typename T, bool TR, int TB, int BT>
+__global__ void __launch_bounds__(BT, BT == FMM_BT_M2L32 ? 2 : 1) k_fmm_m2l_batch(int n_ck, int p, int q, long long jpsize,
                                                           const int* __restrict__ btab,
                                                           const int* __restrict__ ck_b, const int* __restrict__ ck_e,
                                                           const int* __restrict__ perm, const int* __restrict__ m2l_t,
@@ -829,7 +871,7 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
     const int u0 = ck_b[ck], u1 = ck_e[ck];
     for (int ub = u0; ub < u1; ub += TB) {
         const int nt = min(TB, u1 - ub);
-        for (int b = threadIdx.x >> 5; b < TB; b += FMM_BT / 32) {
+        for (int b = threadIdx.x >> 5; b < TB; b += BT / 32) {
             const int lane = threadIdx.x & 31;
             if (b < nt) {
                 const int u = perm ? perm[ub + b] : ub + b;
@@ -848,9 +890,10 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
         __syncthreads();
         int dmax = 0;
         for (int b = 0; b < nt; ++b) dmax = max(dmax, h.pin[b]);
-        batch_load<T, TB>(h, X, a.V, nbp, nbpp, p, TR);
+        batch_prefetch<T, TB>(coax, h, p, q);
+        batch_load<T, TB>(h, btab, X, a.V, nbp, nbpp, p, TR);
         const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
-        batch_translate<T, TB>(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
+        batch_translate<T, TB>(a.JP, coax, h, btab, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
         const int nd2 = h.poff[d2 + 1];
         for (int i = threadIdx.x; i < nd2; i += blockDim.x) {
             T s = a.acc[i];
@@ -859,10 +902,7 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_m2l_batch(int n_ck, int p, int q
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < nbp; i += blockDim.x) {
-        const int l = deg_of(i);
-        part[(size_t)ck * nbp + i] = a.acc[h.poff[l] + i - l * l];
-    }
+    for (int i = threadIdx.x; i < nbp; i += blockDim.x) part[(size_t)ck * nbp + i] = a.acc[__ldg(btab + FMM_GTAB_UNPAD + i)];
 }
 
 // Tree passes, FMM_TB translations per CTA, nodes [first, first + count) of one level.
@@ -917,17 +957,18 @@ __global__ void __launch_bounds__(FMM_BT) k_fmm_tree_batch(int first, int count,
     }
     __syncthreads();
     // forward inputs have degree pin (M2M) or p (L2L); transposed inputs degree p
-    batch_load<T, TB>(h, X, a.V, nbp, nbpp, p, TR);
+    batch_prefetch<T, TB>(coax, h, p, q);
+    batch_load<T, TB>(h, btab, X, a.V, nbp, nbpp, p, TR);
     int dmax = 0;
     for (int b = 0; b < TB; ++b) dmax = max(dmax, h.pin[b]);
     const int d1 = TR ? p : dmax, d2 = TR ? dmax : p;
-    batch_translate<T, TB>(a.JP, coax, h, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
+    batch_translate<T, TB>(a.JP, coax, h, btab, a.ang, p, TR, d1, d2, a.V, a.W, nbpp);
     // combine and write (each node owned by one thread per coefficient: fixed order)
     for (int e = threadIdx.x; e < per * nbp; e += blockDim.x) {
         const int g = e / nbp, i = e - g * nbp;
         const int k = k0 + g;
         if (k >= first + count) continue;
-        const int l = deg_of(i), pi = h.poff[l] + i - l * l;
+        const int pi = __ldg(btab + FMM_GTAB_UNPAD + i);
         if (pairs) {
             if (child0[k] < 0) continue;
             X[(size_t)k * nbp + i] = a.W[(size_t)(2 * g) * nbpp + pi] + a.W[(size_t)(2 * g + 1) * nbpp + pi];
@@ -1250,7 +1291,7 @@ static ddlpb_status fmm_prepare(ddlpb_ctx* c, FmmOps<T>& O) {
     DDLPB_TRY(ctx_alloc(c, &O.JP, Jp.size()));
     DDLPB_CK(c, cudaMemcpyAsync(O.JP, Jp.data(), sizeof(T) * Jp.size(), cudaMemcpyHostToDevice, st));
     std::vector<int> bt;
-    fmm_batch_tables(p, bt);
+    fmm_batch_tables(p, F.q, bt);
     DDLPB_TRY(ctx_alloc(c, &O.btab, bt.size()));
     DDLPB_CK(c, cudaMemcpyAsync(O.btab, bt.data(), sizeof(int) * bt.size(), cudaMemcpyHostToDevice, st));
     DDLPB_TRY(ctx_alloc(c, &O.coax, std::max<long long>(F.coax_size, 1)));
@@ -1292,7 +1333,7 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     const int p = F.p, q = F.q, nbp = (p + 1) * (p + 1), M = c->M, L = c->lmax;
     cudaStream_t st = c->stream;
     const bool f32 = sizeof(T) == 4;
-    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB;
+    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB, BTM = sizeof(T) == 4 ? FMM_BT_M2L32 : FMM_BT;
     const size_t sm0 = fmm_batch_smem<T, FMM_TB>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T, TBM>(p, O.jpsize, 1);
     {
         KernelTimer kt(c, "fmm_tree", f32, 2);
@@ -1309,8 +1350,8 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     }
     if (F.n_ck > 0) {
         KernelTimer kt(c, "fmm_m2l", f32);
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, false, TBM>, sm1)));
-        k_fmm_m2l_batch<T, false, TBM><<<F.n_ck, FMM_BT, sm1, st>>>(F.n_ck, p, q, O.jpsize, O.btab, F.ck_b, F.ck_e, nullptr, F.m2l_t,
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, false, TBM, BTM>, sm1)));
+        k_fmm_m2l_batch<T, false, TBM, BTM><<<F.n_ck, BTM, sm1, st>>>(F.n_ck, p, q, O.jpsize, O.btab, F.ck_b, F.ck_e, nullptr, F.m2l_t,
                                                                 F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP, O.coax,
                                                                 O.Mx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l");
@@ -1350,7 +1391,7 @@ ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
     const int p = F.p, q = F.q, M = c->M, L = c->lmax, N = c->N;
     cudaStream_t st = c->stream;
     const bool f32 = sizeof(T) == 4;
-    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB;
+    constexpr int TBM = sizeof(T) == 4 ? FMM_TB_M2L32 : FMM_TB, BTM = sizeof(T) == 4 ? FMM_BT_M2L32 : FMM_BT;
     const size_t sm0 = fmm_batch_smem<T, FMM_TB>(p, O.jpsize, 0), sm1 = fmm_batch_smem<T, TBM>(p, O.jpsize, 1);
     {
         KernelTimer kt(c, "fmm_tree", f32, 2);
@@ -1368,8 +1409,8 @@ ddlpb_status fmm_adjoint(ddlpb_ctx* c, OpSet<T>& S, const T* c_ext, T* nu) {
     }
     if (F.n_ckT > 0) {
         KernelTimer kt(c, "fmm_m2l_T", f32);
-        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, true, TBM>, sm1)));
-        k_fmm_m2l_batch<T, true, TBM><<<F.n_ckT, FMM_BT, sm1, st>>>(F.n_ckT, p, q, O.jpsize, O.btab, F.ckT_b, F.ckT_e, F.m2lT_k,
+        DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_m2l_batch<T, true, TBM, BTM>, sm1)));
+        k_fmm_m2l_batch<T, true, TBM, BTM><<<F.n_ckT, BTM, sm1, st>>>(F.n_ckT, p, q, O.jpsize, O.btab, F.ckT_b, F.ckT_e, F.m2lT_k,
                                                                 F.m2l_t, F.m2l_s, F.m2l_off, F.child0, F.node_g, O.JP,
                                                                 O.coax, O.Lx, O.part);
         DDLPB_LAUNCHED(c, "fmm_m2l_T");
