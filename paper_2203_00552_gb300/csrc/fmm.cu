@@ -366,32 +366,46 @@ __global__ void k_fmm_leaf_pot(int N, int nb, int L, int p, T kappa, const int* 
     const int nbp = (p + 1) * (p + 1);
     T* Li = (T*)smraw;
     T* rad = Li + nbp;
+    T* part = rad + (size_t)(L + 1) * bd;
     const int i = blockIdx.x;
     const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
     if (cnt == 0) return;
     for (int k = tid; k < nbp; k += bd) Li[k] = Lx[(size_t)leaf_node[i] * nbp + k];
-    __syncthreads();
     const double4 a = sph64[i];
     const int k0 = near_ptr[i], k1 = near_ptr[i + 1];
-    for (int t = t0 + tid; t < t0 + cnt; t += bd) {
-        const int n = ext_p[t] % N;
-        const T* Y = Yp + (size_t)n * nbp;
-        T acc = 0;
-        for (int k = 0; k < nbp; ++k) acc += Li[k] * __ldg(Y + k);
-        const double4 s = leb64[n];
-        for (int kk = k0; kk < k1; ++kk) {
-            const int j = near_j[kk];
-            const double4 b = sph64[j];
-            const T dx = (T)(a.x - b.x + a.w * s.x), dy = (T)(a.y - b.y + a.w * s.y), dz = (T)(a.z - b.z + a.w * s.z);
-            const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
-            radial<T>(2, L, rho, (T)b.w, kappa, Khinv + (size_t)j * (L + 2), rad + tid, nullptr, bd);
-            const T* m = mu + (size_t)j * nb;
-            T v = 0;
-            ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
-                          [&](int idx, int l, T yv) { v += __ldg(m + idx) * rad[tid + l * bd] * yv; });
-            acc += v;
+    // S slices of the near sources per point (thread = point pi of the round, slice sl), partial
+    // sums added in slice order
+    const int S = max(1, min(bd / cnt, k1 - k0)), P = bd / S;
+    const int pi = tid % P, sl = tid / P;
+    for (int base = 0; base < cnt; base += P) {
+        __syncthreads();
+        const int t = t0 + base + pi;
+        T v = 0;
+        if (sl < S && base + pi < cnt) {
+            const double4 sn = leb64[ext_p[t] % N];
+            for (int kk = k0 + sl; kk < k1; kk += S) {
+                const int j = near_j[kk];
+                const double4 b = sph64[j];
+                const T dx = (T)(a.x - b.x + a.w * sn.x), dy = (T)(a.y - b.y + a.w * sn.y),
+                        dz = (T)(a.z - b.z + a.w * sn.z);
+                const T rho = sqrt(dx * dx + dy * dy + dz * dz), inv = (T)1 / rho;
+                radial<T>(2, L, rho, (T)b.w, kappa, Khinv + (size_t)j * (L + 2), rad + tid, nullptr, bd);
+                const T* m = mu + (size_t)j * nb;
+                T w = 0;
+                ylm_stream<T>(L, dx * inv, dy * inv, dz * inv, yt,
+                              [&](int idx, int l, T yv) { w += __ldg(m + idx) * rad[tid + l * bd] * yv; });
+                v += w;
+            }
         }
-        phi[t] = acc;
+        part[tid] = v;
+        __syncthreads();
+        if (sl == 0 && base + pi < cnt) {
+            const T* Y = Yp + (size_t)(ext_p[t] % N) * nbp;
+            T acc = 0;
+            for (int k = 0; k < nbp; ++k) acc += Li[k] * __ldg(Y + k);
+            for (int q = 0; q < S; ++q) acc += part[q * P + pi];
+            phi[t] = acc;
+        }
     }
 }
 
@@ -444,14 +458,15 @@ __global__ void k_fmm_leaf_adj(int N, int nb, int L, int p, int q, T kappa, cons
     for (int k = tid; k < nw * nb; k += bd) acc[k] = 0;
     for (int k = tid; k < L + 2; k += bd) kh[k] = Khinv[(size_t)j * (L + 2) + k];
     __syncthreads();
-    for (int kk = nearT_ptr[j]; kk < nearT_ptr[j + 1]; ++kk) {
+    // warp w takes the near targets w, w + nw, ... and its lanes their points, 32 at a time
+    for (int kk = nearT_ptr[j] + warp; kk < nearT_ptr[j + 1]; kk += nw) {
         const int i = nearT_i[kk];
         const double4 a = sph64[i];
         const int t0 = ext_ptr[i], cnt = ext_ptr[i + 1] - t0;
-        for (int base = 0; base < cnt; base += bd) {
+        for (int base = 0; base < cnt; base += 32) {
             T dx = (T)b.w, dy = 0, dz = 0, c = 0;
-            if (base + tid < cnt) {
-                const int t = t0 + base + tid;
+            if (base + lane < cnt) {
+                const int t = t0 + base + lane;
                 const double4 s = leb64[ext_p[t] % N];
                 dx = (T)(a.x - b.x + a.w * s.x);
                 dy = (T)(a.y - b.y + a.w * s.y);
@@ -1369,7 +1384,7 @@ ddlpb_status fmm_potential(ddlpb_ctx* c, OpSet<T>& S, const T* mu, T* phi_ext) {
     }
     if (c->E > 0) {
         KernelTimer kt(c, "fmm_near", f32, 2);
-        const size_t sm2 = sizeof(T) * ((size_t)nbp + (size_t)(L + 1) * 128);
+        const size_t sm2 = sizeof(T) * ((size_t)nbp + (size_t)(L + 2) * 128);
         DDLPB_TRY((fmm_smem_attr<T>(c, k_fmm_leaf_pot<T, V4>, sm2)));
         k_fmm_leaf_pot<T, V4><<<M, 128, sm2, st>>>(c->N, c->nb, L, p, (T)c->kappa, c->ext_ptr, c->ext_p, c->sph,
                                                    c->leb, F.leaf_node, O.Lx, O.Yp, F.near_ptr, F.near_j, mu, S.Khinv,
