@@ -4,9 +4,13 @@
         grid is exact to degree 2 lmax (the convergence study of Sec. 4); FP64, tolerance 1e-11.
   size: atoms/s of a whole step (setup, both solves, energy, forces; mixed precision, tolerance
         1e-8) for globules of M atoms at one (lmax, grid): the growth of the cost with M.
+  fmm:  for every (admissibility theta, order p): the FP64 FMM solution against the FP64 direct
+        one (energy and forces, tolerance 1e-11; the p_max study of Sec. 4), and the wall time of
+        one step of the mixed form (tolerance 1e-8) after one warm-up step.
 
     python -m paper_2203_00552_gb300.sweeps lmax --atoms 100 --lmax 2 4 6 8 10 12 --grid 302 590 770
     python -m paper_2203_00552_gb300.sweeps size --lmax 6 --grid 110 --atoms 100 300 1000 3000
+    python -m paper_2203_00552_gb300.sweeps fmm --workload globule1000_sas --theta 0.5 0.4 0.3 0.25 --order 12 16 20
 
 Each prints one JSON line.
 """
@@ -89,6 +93,45 @@ def size_sweep(sizes, seed: int, lmax: int, grid: int):
             "rows": rows}
 
 
+def fmm_sweep(workload: str, thetas, orders):
+    import numpy as np
+    import torch
+
+    from . import _binding as B
+    w = synth.workload(workload)
+    opts = dict(gmres_restart=300, precond_tol=0.4, max_iter=4000)
+
+    def ctx(**kw):
+        return B.Context(w["centres"], w["radii"], w["charges"], w["eps_solvent"], w["kappa"], w["lmax"],
+                         w["n_lebedev"], surface=w["surface"], **dict(opts, **kw))
+
+    def energy_forces(**kw):
+        c = ctx(**kw)
+        try:
+            c.solve()
+            c.adjoint()
+            return c.energy(), c.forces(), c.info()
+        finally:
+            c.close()
+
+    E0, F0, _ = energy_forces(precision=B.DDLPB_FP64, tol=1e-11, fmm_order=0)
+    rows = []
+    for theta in thetas:
+        for p in orders:
+            E, F, info = energy_forces(precision=B.DDLPB_FP64, tol=1e-11, fmm_order=p, fmm_theta=theta)
+            energy_forces(precision=B.DDLPB_MIXED, tol=1e-8, fmm_order=p, fmm_theta=theta)   # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            energy_forces(precision=B.DDLPB_MIXED, tol=1e-8, fmm_order=p, fmm_theta=theta)
+            torch.cuda.synchronize()
+            rows.append({"theta": theta, "order": p, "energy_rel_err": abs(E - E0) / abs(E0),
+                         "force_rel_err": float(np.linalg.norm(F - F0) / np.linalg.norm(F0)),
+                         "force_max_abs_err": float(np.abs(F - F0).max()), "mixed_step_s": time.perf_counter() - t0,
+                         "m2l": info["fmm_m2l"], "near_pairs": info["fmm_near_pairs"]})
+            print(json.dumps(rows[-1]), flush=True)
+    return {"sweep": "fmm", "workload": workload, "energy_direct_hartree": E0, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="what", required=True)
@@ -102,11 +145,17 @@ def main():
     b.add_argument("--seed", type=int, default=4)
     b.add_argument("--lmax", type=int, default=6)
     b.add_argument("--grid", type=int, default=110)
+    f = sub.add_parser("fmm")
+    f.add_argument("--workload", default="globule1000_sas")
+    f.add_argument("--theta", type=float, nargs="+", default=[0.5, 0.4, 0.3, 0.25])
+    f.add_argument("--order", type=int, nargs="+", default=[12, 16, 20])
     args = ap.parse_args()
     if args.what == "lmax":
         out = lmax_sweep(args.atoms, args.seed, sorted(args.lmax), args.grid)
-    else:
+    elif args.what == "size":
         out = size_sweep(args.atoms, args.seed, args.lmax, args.grid)
+    else:
+        out = fmm_sweep(args.workload, args.theta, args.order)
     print(json.dumps(out), flush=True)
 
 
