@@ -82,6 +82,24 @@ def test_setup_rejects_bad_input_before_touching_the_gpu(lib):
         assert e.value.status == 1
 
 
+def test_setup_rejects_bad_solver_and_fmm_options(lib):
+    """Options outside their documented ranges (include/ddlpb.h) are refused with EINVAL before
+    any device work: FMM order below lmax + 1 or above 21, admissibility ratio outside (0, 1),
+    restart length outside [1, 2000], preconditioner tolerance outside (0, 1]."""
+    import numpy as np
+    c = np.zeros((2, 3))
+    c[1, 0] = 3.0
+    r = np.array([2.0, 2.0])
+    q = np.array([0.1, -0.1])
+    bad = [dict(fmm_order=4), dict(fmm_order=22), dict(fmm_order=8, fmm_theta=1.0), dict(fmm_order=8, fmm_theta=0.0),
+           dict(gmres_restart=2001), dict(gmres_restart=0), dict(precond_tol=1.5), dict(eta=0.0)]
+    for kw in bad:
+        with pytest.raises(_binding.DDLPBError) as e:
+            _binding.Context(c, r, q, 78.54, 0.05, 4, 110, **kw)
+        assert e.value.status == 1, kw
+        assert str(e.value), kw
+
+
 def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(_binding, "_lib", None)
     monkeypatch.setattr(_binding, "LIB_PATH", "/nonexistent/libddlpb.so")
