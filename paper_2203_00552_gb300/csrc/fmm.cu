@@ -29,9 +29,9 @@
 // operator set (HBM holds them easily); the rotations are applied on the fly, a batch of
 // translations per CTA, with J in shared memory.
 //
-// Every pass gathers (one warp per target or per chunk of a target's list, partial sums added
-// in a fixed order), so the operator is deterministic: the mixed-precision refinement evaluates
-// it repeatedly and needs the same rounding each time.
+// Every pass gathers (a CTA per chunk of a target's M2L list, per group of tree nodes, or per
+// leaf sphere; partial sums added in a fixed order), so the operator is deterministic: the
+// mixed-precision refinement evaluates it repeatedly and needs the same rounding each time.
 #include <cub/cub.cuh>
 
 #include <algorithm>
