@@ -110,7 +110,8 @@ def reference_arm(args, w):
     value = atoms / dt
     cores = os.cpu_count()
     sample = ("oracle energy+forces (dense LU, FP64 numpy) on the first %d atoms of the %d-atom globule, "
-              "lmax %d, %d Lebedev points" % (atoms, w["n"], w["lmax"], w["n_lebedev"]))
+              "lmax %d, %d Lebedev points; its cost grows like M^3 (dense solve) and M^2 (coupling), so this "
+              "is the rate on the sample, not on the whole workload" % (atoms, w["n"], w["lmax"], w["n_lebedev"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -414,7 +415,8 @@ def main():
         dt = oracle_sample(w, atoms)
         cpu = {"value": atoms / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "oracle energy+forces (dense LU, FP64 numpy) on the first %d atoms of this workload, "
-                         "%.1f s" % (atoms, dt)}
+                         "%.1f s; its cost grows like M^3 (dense solve) and M^2 (coupling), so this is the rate on "
+                         "the sample, not on the whole workload" % (atoms, dt)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
