@@ -3,7 +3,8 @@
 Default workload (named in config.workload): `globule1000_sas`, the 1000-atom globule (chain
 growth rule, then compacted onto the 18 A ball, seed 1), SAS radii (U[1.2, 2.0] A + 1.4 A
 probe), charges U[-0.5, 0.5] e with zero net charge, eps = 78.54, kappa = 0.104 1/A, lmax = 8,
-302-point Lebedev grid, the coupling's far field by the FMM of order 16, outer tolerance 1e-8
+302-point Lebedev grid, the coupling's far field by the FMM of order 16 (admissibility ratio
+0.4), outer tolerance 1e-8
 (FP64 relative residual).  The 10,000-atom globule (lmax 10, 590 points, FMM order 20;
 `--workload globule10000`) fits one GPU, but its preconditioned system needs thousands of
 Krylov iterations (their count grows with the atom count and lmax), far beyond a bench run.
@@ -14,7 +15,7 @@ times the plain FP64 path.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own copy of the workload (replicas:
-one molecule does not shard in this build); value = all atoms / max time.
+one molecule is not split across GPUs); value = all atoms / max time.
 """
 from __future__ import annotations
 
