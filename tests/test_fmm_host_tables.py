@@ -114,3 +114,50 @@ def test_gaunt_sums_match_quadrature(tables):
         for mm in ((m, -m) if m > 0 else (0,)):
             want = 4 * np.pi * yb0_ez * np.sum(w * Y[:, l * l + l + mm] * Y[:, a * a + a + mm] * Y[:, b * b + b])
             assert abs(g - want) < 1e-12 * max(1.0, abs(want)), (m, l, a, j, mm, g, want)
+
+
+def test_translation_with_JT_only_equals_the_rotation_sequence(tables):
+    """The batched kernels translate as Rz(a) J Rz(b) J^T Z J Rz(-b) J^T Rz(-a) but form every
+    product with J as S J^T S and fold the two S into the neighbouring steps; the folded sequence
+    gives the same operator (Z any m-preserving coaxial map, same block for +m and -m)."""
+    P = 6
+    nb = (P + 1) ** 2
+    J = np.array(tables["J"])
+    Jf = np.zeros((nb, nb))
+    o = 0
+    for l in range(P + 1):
+        n = 2 * l + 1
+        Jf[l * l:l * l + n, l * l:l * l + n] = J[o:o + n * n].reshape(n, n)
+        o += n * n
+    lidx = np.array([int(np.sqrt(i)) for i in range(nb)])
+    midx = np.arange(nb) - lidx * lidx - lidx
+    S = np.diag(np.where(midx < 0, -1.0, 1.0))
+
+    def Rz(ang, s):
+        R = np.eye(nb)
+        for i in range(nb):
+            l, m = lidx[i], midx[i]
+            if m > 0:
+                j = l * l + l - m
+                c, sn = np.cos(m * ang), s * np.sin(m * ang)
+                R[i, i], R[i, j], R[j, i], R[j, j] = c, -sn, sn, c
+        return R
+
+    rng = np.random.default_rng(2)
+    Z = np.zeros((nb, nb))
+    for m in range(P + 1):
+        for l in range(m, P + 1):
+            for a in range(m, P + 1):
+                v = rng.normal()
+                Z[a * a + a + m, l * l + l + m] = v
+                if m > 0:
+                    Z[a * a + a - m, l * l + l - m] = v
+    al, be = 0.7, 1.9
+    x = rng.normal(size=nb)
+    plain = Rz(al, 1) @ Jf @ Rz(be, 1) @ Jf.T @ Z @ Jf @ Rz(be, -1) @ Jf.T @ Rz(al, -1) @ x
+    v = Jf.T @ (Rz(al, -1) @ x)
+    v = Jf.T @ (S @ (Rz(be, -1) @ v))        # rotation with its output flipped, then J^T
+    v = Jf.T @ (Z @ (S @ v))                 # the coaxial step reads the flipped input
+    v = Jf.T @ (S @ (Rz(be, 1) @ v))
+    folded = Rz(al, 1) @ (S @ v)             # the last rotation reads the flipped input
+    assert np.abs(plain - folded).max() < 1e-12 * np.abs(plain).max()
