@@ -434,6 +434,7 @@ def main():
                 "solver": {"outer": info["solve_iterations"], "adjoint_outer": info["adjoint_iterations"],
                            "refinement": info["refinement_steps"], "residual": info["solve_residual"],
                            "adjoint_residual": info["adjoint_residual"], "external_points": info["n_external"],
+                           "external_fraction": info["n_external"] / float(M * w["n_lebedev"]),
                            "hits": info["n_hits"], "sources": info["n_sources"], "fmm_m2l": info["fmm_m2l"],
                            "fmm_near_pairs": info["fmm_near_pairs"], "fmm_nodes": info["fmm_nodes"]},
                 "energy_hartree": float(e_out.item())}
